@@ -1,0 +1,440 @@
+#!/usr/bin/env python
+"""Throughput of the multiscale-thermalization hot path on GB300.
+
+Workload (one step): one compound sweep of a 32^4 SU(3) Wilson lattice at
+beta = 6.0 -- one Cabibbo-Marinari heat-bath sweep (N_hb = 1) followed by
+four overrelaxation sweeps on the checkerboard schedule -- plus the FP64
+average plaquette of the result, as the rethermalisation stage of the
+multiscale method runs it.  Links are FP32 with 12-real (two-row)
+compression; reductions are FP64.  The value is link updates per second
+over the whole job (5 x 4V updates per step per GPU).
+
+Also measured in the same run: the HMC gauge force + momentum update in
+algorithmic GB/s, the plain FP64 GPU path and the 18-real FP32 path
+(link updates/s), an end-to-end number through the C ABI with the step's
+input links copied from pinned host memory and the plaquette read back,
+and the FP64 CPU oracle on a bounded sample (cpu_baseline).
+
+Multi-GPU: replicas only (independent lattices, one per rank; no
+collective on the data path).  `--impl reference` times the CPU oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "link updates/s + force GB/s, 32^4 SU(3), vs plain FP64 GPU; % HBM roofline"
+UNIT = "link updates/s"
+LINK_BYTES = {"f64": 144, "f32": 72, "f32c12": 48}
+REAL_BYTES = {"f64": 8, "f32": 4, "f32c12": 4}
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["mgq", "reference"], default="mgq")
+    p.add_argument("--prec", choices=["f64", "f32", "f32c12"], default="f32c12")
+    p.add_argument("--dims", default="32,32,32,32")
+    p.add_argument("--beta", type=float, default=6.0)
+    p.add_argument("--n-or", type=int, default=4)
+    p.add_argument("--therm", type=int, default=30, help="untimed thermalisation sweeps before timing")
+    p.add_argument("--no-extras", action="store_true", help="skip the FP64/FP32 comparison legs")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload_config(args, dims):
+    V = 1
+    for d in dims:
+        V *= d
+    return {
+        "workload": f"{'x'.join(map(str, dims))} SU(3) Wilson beta={args.beta}: 1 heat-bath (Creutz, N_hb=1) + "
+                    f"{args.n_or} overrelaxation sweeps + FP64 plaquette per step",
+        "lattice": dims,
+        "beta": args.beta,
+        "n_or": args.n_or,
+        "link_format": args.prec,
+        "link_updates_per_step_per_gpu": (1 + args.n_or) * 4 * V,
+        "l2": "no flush: the link field (%.0f MB) is larger than the 129 MB L2" % (4 * V * LINK_BYTES[args.prec] / 1e6),
+        "parallelism": "replicas",
+    }
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Dist:
+    def __init__(self, world, rank, local, use_cuda):
+        self.world, self.rank, self.local = world, rank, local
+        self.pg = None
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group("nccl" if use_cuda else "gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+
+        t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def src_hash() -> str:
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1510_04675_gb300", "csrc", "*")) +
+                   glob.glob(os.path.join(ROOT, "include", "*.h")))
+    for f in files:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(kernel: str, workload_tag: str):
+    """DRAM bytes per launch recorded by an ncu capture summary under profiles/,
+    if it was taken on the current kernel sources."""
+    cur = src_hash()
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.txt"))):
+        for line in open(f):
+            t = line.split()
+            if len(t) >= 7 and t[0] == "traffic_bytes_per_launch" and t[1] == kernel and t[2] == workload_tag \
+                    and t[4] == "src_hash":
+                if t[5] == cur:
+                    return float(t[3])
+    return None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(dims, beta, seconds_hint=20.0):
+    """Time the FP64 oracle on one full compound sweep (1 HB + 4 OR) of a hot-start lattice."""
+    import oracle
+
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    U = oracle.init_links(dims, 1, seed=7)
+    V = U.shape[0]
+    t0 = time.perf_counter()
+    oracle.heatbath_sweep(U, dims, beta, 7, 0, 1, 1)
+    for _ in range(4):
+        oracle.overrelax_sweep(U, dims)
+    dt = time.perf_counter() - t0
+    return {"value": 5 * 4 * V / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one compound sweep (1 HB + 4 OR) of a hot-start {'x'.join(map(str, dims))} lattice, "
+                      f"{5 * 4 * V} link updates in {dt:.2f} s (FP64, OpenMP)"}
+
+
+def run_reference(args, dims, world, rank):
+    """CPU oracle as the reference arm: each step is the mu = step mod 4 slice of a compound sweep."""
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    U = oracle.init_links(dims, 1, seed=7)
+    V = U.shape[0]
+
+    def step(i):
+        mu = i % 4
+        for par in (0, 1):
+            oracle.heatbath_subsweep(U, dims, args.beta, 7, 0, i, 1, mu, par)
+        for _ in range(args.n_or):
+            for par in (0, 1):
+                oracle.overrelax_subsweep(U, dims, mu, par)
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    dt = time.perf_counter() - t0
+    per_step = (1 + args.n_or) * V  # one mu, both parities
+    value = per_step * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload_config(args, dims), link_format="f64 (oracle)",
+                       sample="each step: one direction mu of a compound sweep (2 HB + 2 x n_or OR sub-sweeps)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} steps of {per_step} link updates each"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def ev():
+    import torch
+
+    return torch.cuda.Event(enable_timing=True)
+
+
+def time_sweeps(api, lat, beta, n_or, steps, sweep0):
+    """Link updates/s of `steps` compound sweeps (device-resident)."""
+    import torch
+
+    for i in range(2):
+        api.mgq_update_sweeps(lat, beta, sweep0 + i, 1, 1, n_or)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record()
+    api.mgq_update_sweeps(lat, beta, sweep0 + 2, steps, 1, n_or)
+    b.record()
+    torch.cuda.synchronize()
+    return (1 + n_or) * 4 * lat.volume * steps / (a.elapsed_time(b) * 1e-3)
+
+
+def run_mgq(args, dims, world, rank, local):
+    import torch
+
+    from paper_1510_04675_gb300 import api
+    from paper_1510_04675_gb300 import build as mgq_build
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU for --impl mgq")
+    torch.cuda.set_device(local)
+    mgq_build.build()
+    dist = Dist(world, rank, local, True)
+    V = 1
+    for d in dims:
+        V *= d
+    beta, n_or, K, W = args.beta, args.n_or, args.steps, args.warmup
+
+    lat = api.Lattice(dims, args.prec, seed=1234, lattice_id=rank, with_mom=True)
+    api.mgq_init_links(lat, 1)
+    api.mgq_update_sweeps(lat, beta, 0, args.therm, 1, n_or)
+    plaq_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    sweep0 = 1000
+
+    hb_ev, or_ev = [], []
+
+    def step(i, record):
+        if record:
+            e = (ev(), ev(), ev())
+            e[0].record()
+        api.mgq_heatbath_sweep(lat, beta, sweep0 + i, 1)
+        if record:
+            e[1].record()
+        for _ in range(n_or):
+            api.mgq_overrelax_sweep(lat)
+        if record:
+            e[2].record()
+            hb_ev.append((e[0], e[1]))
+            or_ev.append((e[1], e[2]))
+        api.mgq_plaquette(lat, out=plaq_dev)
+
+    for i in range(W):
+        step(i, False)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    t0, t1 = ev(), ev()
+    t0.record()
+    for i in range(K):
+        step(W + i, True)
+    t1.record()
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    t_local = t0.elapsed_time(t1) * 1e-3
+    t = dist.max(t_local)
+    updates_per_step = (1 + n_or) * 4 * V
+    value = world * K * updates_per_step / t
+
+    # dominant kernel and its roofline (per-launch algorithmic bytes / average launch time)
+    hb_ms = sum(a.elapsed_time(b) for a, b in hb_ev) / (8 * K)
+    or_ms = sum(a.elapsed_time(b) for a, b in or_ev) / (8 * n_or * K)
+    lb = LINK_BYTES[args.prec]
+    bytes_per_launch = (V // 2) * 9 * lb  # 9 link transfers per link update, V/2 updates per launch
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_src = "measured" if peaks else "fallback"
+    tag = "x".join(map(str, dims)) + "_" + args.prec
+    kernels = {"k_heatbath": hb_ms, "k_overrelax": or_ms}
+    share = {"k_heatbath": 8 * hb_ms, "k_overrelax": 8 * n_or * or_ms}
+    dom = max(share, key=share.get)
+
+    def roof(name, ms):
+        ach = bytes_per_launch / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": traffic_from_profiles(name, tag), "kernel": name, "ms_per_launch": ms,
+                "algorithmic_bytes_per_launch": bytes_per_launch, "peak_source": peak_src}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": 1e3 * t / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.prec != "f64" else "f64", "data": "synthetic (hot start, thermalised in-run)",
+        "config": workload_config(args, dims),
+        "roofline": roof(dom, kernels[dom]),
+        "roofline_heatbath": roof("k_heatbath", hb_ms),
+        "gpu_launches": K * (8 + 8 * n_or + 2),
+        "clocks": clocks,
+    }
+
+    # HMC force + momentum update (algorithmic GB/s: links once + P read and written)
+    try:
+        F = lat.new_alg_field()
+        for _ in range(3):
+            api.mgq_hmc_force(lat, beta, F)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        nf = 20
+        a.record()
+        for _ in range(nf):
+            api.mgq_hmc_force(lat, beta, F)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / nf
+        fb = 4 * V * (lb + 8 * REAL_BYTES[args.prec])
+        out["force_gbs"] = fb / (ms * 1e-3) / 1e9
+        out["force_ms"] = ms
+        out["force_roofline_frac"] = out["force_gbs"] / peak
+    except Exception as e:  # noqa: BLE001 - reported, not hidden
+        out["force_gbs"] = None
+        out["force_error"] = str(e)[:200]
+
+    # end to end through the C ABI: pinned host links in, plaquette (host) out
+    import numpy as np
+
+    host_links = lat.links.cpu().pin_memory()
+    plaq_host = np.zeros(1)
+    ne = max(3, min(K, 10))
+    s = torch.cuda.current_stream()
+    for i in range(2):
+        lat.links.copy_(host_links, non_blocking=True)
+        api.mgq_update_sweeps(lat, beta, sweep0 + 5000 + i, 1, 1, n_or, plaq_out=plaq_host)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for i in range(ne):
+        lat.links.copy_(host_links, non_blocking=True)
+        api.mgq_update_sweeps(lat, beta, sweep0 + 6000 + i, 1, 1, n_or, plaq_out=plaq_host)
+    s.synchronize()
+    we = time.perf_counter() - w0
+    e2e_t = dist.max(we)
+    out["e2e"] = {"value": world * ne * updates_per_step / e2e_t, "unit": UNIT,
+                  "h2d_bytes_per_step": int(host_links.numel()), "d2h_bytes_per_step": 8}
+
+    if not args.no_extras and rank == 0:
+        for prec, key in [("f64", "fp64_plain"), ("f32", "fp32_18real")]:
+            l2 = api.Lattice(dims, prec, seed=99)
+            api.mgq_init_links(l2, 1)
+            api.mgq_update_sweeps(l2, beta, 0, 2, 1, n_or)
+            r = time_sweeps(api, l2, beta, n_or, 2 if prec == "f64" else 5, 10)
+            out[key + "_link_updates_per_s"] = r
+            del l2
+        out["speedup_vs_fp64"] = (value / world) / out["fp64_plain_link_updates_per_s"]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_sample(dims, beta)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    dist.close()
+    return 0
+
+
+def main():
+    args = parse_args()
+    dims = [int(v) for v in args.dims.split(",")]
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, dims, world, rank)
+    return run_mgq(args, dims, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

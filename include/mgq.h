@@ -1,0 +1,210 @@
+/*
+ * mgq.h -- C ABI of libmgq, the GB300 (sm_103a) hot path of the multiscale
+ * thermalization of pure SU(3) Yang-Mills theory (Endres, Brower, Detmold,
+ * Orginos, Pochinsky, "Multiscale Monte Carlo equilibration: Pure Yang-Mills
+ * theory", arXiv:1510.04675).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Ownership: the caller allocates every buffer (links, momenta, workspace,
+ *   outputs) and keeps it alive until the work queued on `stream` is done.
+ *   The library allocates no device memory.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All
+ *   work is queued asynchronously on it.  An entry point that writes a
+ *   result to a HOST pointer synchronises `stream` before returning; output
+ *   pointers may be host or device memory and are classified with
+ *   cudaPointerGetAttributes.
+ * Errors: every entry point returns an mgq_status and never aborts; the
+ *   message of the last failure on the calling thread is mgq_last_error().
+ *   Argument errors are detected before any work is queued.
+ * Lattice (Sec. III): D = 4 hypercube with extents dims[0..3] (all even,
+ *   >= 2), periodic boundary conditions, V = dims[0]*dims[1]*dims[2]*dims[3]
+ *   sites.  Site (x0,x1,x2,x3) has lexicographic index
+ *   x0 + L0*(x1 + L1*(x2 + L2*x3)) and parity (x0+x1+x2+x3) mod 2.
+ *
+ * Device link layout (owned by the caller, written by the library)
+ * ----------------------------------------------------------------
+ *   links[mu][parity][plane][h], mu = 0..3, parity = 0..1,
+ *   h = lex/2 in 0..V/2-1, site stride S = mgq_site_stride(dims) >= V/2.
+ *   Each element of a plane is one complex number of the link matrix U_mu(x)
+ *   (re, im adjacent):
+ *     MGQ_F64     : 9 planes (row-major 3x3) of double2   -> 144 B per link
+ *     MGQ_F32     : 9 planes of float2                     ->  72 B per link
+ *     MGQ_F32_C12 : 6 planes (rows 0 and 1) of float2; row 2 is rebuilt as
+ *                   conj(row0 x row1) on every load        ->  48 B per link
+ *   Momenta / Lie-algebra fields: mom[mu][parity][a][h], a = 0..7, the
+ *   coefficients p_a of P = sum_a p_a X_a, X_a = i lambda_a / 2 (Gell-Mann),
+ *   as double (MGQ_F64) or float (MGQ_F32, MGQ_F32_C12).
+ *
+ * Canonical exchange layout (mgq_import_links / mgq_export_links): double
+ *   canon[V][4][3][3][2], site lexicographic, then mu, row, column, re/im.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with
+ *   counter = (site_lex, mu | subgroup<<2 | attempt<<4 | kind<<12,
+ *              lo32(index), hi32(index)),
+ *   key = (lo32(seed), hi32(seed) ^ lattice_id); kind 1 = heat bath,
+ *   2 = hot start, 3 = momenta, 4 = HMC accept; index = sweep or trajectory.
+ *   Results therefore depend only on (seed, lattice_id, index), not on the
+ *   launch configuration.
+ */
+#ifndef MGQ_H
+#define MGQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MGQ_ABI_VERSION 1
+
+typedef enum {
+    MGQ_OK = 0,
+    MGQ_EINVAL = 1,         /* invalid argument (message in mgq_last_error)       */
+    MGQ_ENOMEM = 2,         /* caller-provided workspace too small                */
+    MGQ_ECUDA = 3,          /* a CUDA runtime call or kernel launch failed        */
+    MGQ_EUNSUPPORTED = 4,   /* valid request outside the built scope (e.g. open BC) */
+    MGQ_ETIMEOUT = 5,       /* a bounded device wait gave up                      */
+    MGQ_ENONUNITARY = 6     /* mgq_check_unitarity found a link off SU(3)         */
+} mgq_status;
+
+typedef enum { MGQ_F64 = 0, MGQ_F32 = 1, MGQ_F32_C12 = 2 } mgq_prec;
+typedef enum { MGQ_WILSON = 0 } mgq_action;               /* the paper's action (Sec. III) */
+typedef enum { MGQ_PERIODIC = 0, MGQ_OPEN = 1 } mgq_bc;   /* periodic only (Sec. IV.A)    */
+
+/* One lattice and the caller's device buffers for it. */
+typedef struct mgq_lattice {
+    int32_t dims[4];       /* L0..L3, each even and >= 2                           */
+    int32_t bc[4];         /* mgq_bc per direction; only MGQ_PERIODIC is supported */
+    int32_t prec;          /* mgq_prec: storage and arithmetic format of the links */
+    int32_t action;        /* mgq_action                                           */
+    uint64_t seed;         /* Philox key, low and high words                       */
+    uint32_t lattice_id;   /* xor-ed into the key's high word: one stream per lattice */
+    uint32_t reserved;     /* must be 0                                            */
+    void* links;           /* device, mgq_links_bytes() bytes                       */
+    void* mom;             /* device, mgq_mom_bytes() bytes; HMC only, else NULL   */
+    void* work;            /* device, >= mgq_workspace_bytes() bytes, 256-B aligned */
+    uint64_t work_bytes;   /* size of `work`                                       */
+} mgq_lattice;
+
+/* ---- sizes and diagnostics ------------------------------------------------ */
+int mgq_abi_version(void);
+const char* mgq_status_string(mgq_status s);
+/* Message of the last failing call on this thread ("" if none). */
+const char* mgq_last_error(void);
+/* Per-parity site stride S (elements) for the given extents; 0 if invalid. */
+uint64_t mgq_site_stride(const int32_t dims[4]);
+/* Bytes of the link array, the momentum array and the workspace for `lat`
+ * (only dims and prec are read); 0 if the extents or precision are invalid. */
+uint64_t mgq_links_bytes(const mgq_lattice* lat);
+uint64_t mgq_mom_bytes(const mgq_lattice* lat);
+uint64_t mgq_workspace_bytes(const mgq_lattice* lat);
+
+/* ---- fields ---------------------------------------------------------------- */
+/* Start configurations (Sec. IV.E): start = 0 cold (unit links, the ordered
+ * delta-function start), start = 1 hot (Haar-random SU(3) per link from the
+ * hot-start Philox stream).  Errors: MGQ_EINVAL. */
+mgq_status mgq_init_links(mgq_lattice* lat, int start, void* stream);
+
+/* Copy a field between the canonical FP64 layout (device pointer `canon`,
+ * V*4*18 doubles) and the lattice's own layout.  Import rounds to the
+ * lattice precision (MGQ_F32_C12 keeps rows 0 and 1); export rebuilds
+ * row 2 for MGQ_F32_C12.  Errors: MGQ_EINVAL, MGQ_ECUDA. */
+mgq_status mgq_import_links(mgq_lattice* lat, const double* canon, void* stream);
+mgq_status mgq_export_links(const mgq_lattice* lat, double* canon, void* stream);
+
+/* ---- local updates (Sec. IV.A: Cabibbo-Marinari heat bath with Creutz's
+ *      SU(2) sampler, Brown-Woch overrelaxation, checkerboard schedule) ---- */
+
+/* One heat-bath sweep at coupling beta (Sec. III: beta = 2 Nc / g^2): for
+ * mu = 0..3, parity = 0, 1, every link U_mu(x) of that subset is updated
+ * from its staple: V = U A, for the subgroups (0,1), (0,2), (1,2) up to n_hb
+ * Creutz attempts (1 <= n_hb <= 256), U <- R U, then Gram-Schmidt
+ * reunitarisation.  `sweep` is the RNG index.  Errors: MGQ_EINVAL. */
+mgq_status mgq_heatbath_sweep(mgq_lattice* lat, double beta, uint64_t sweep, int n_hb, void* stream);
+
+/* One (mu, parity) subset of the sweep above.  decisions (device, optional,
+ * uint8[V][4][3] in lexicographic site order) receives for each updated link
+ * and subgroup the accepted attempt index, or 255 if none was accepted. */
+mgq_status mgq_heatbath_subsweep(mgq_lattice* lat, double beta, uint64_t sweep, int n_hb, int mu,
+                                 int parity, uint8_t* decisions, void* stream);
+
+/* One overrelaxation sweep (same schedule; per subgroup the reflection
+ * R = (w/|w|)^2 that keeps Re Tr(U A) unchanged).  No RNG, no beta. */
+mgq_status mgq_overrelax_sweep(mgq_lattice* lat, void* stream);
+
+/* n_sweeps compound sweeps, each 1 heat-bath sweep (RNG index sweep0 + i)
+ * followed by n_or overrelaxation sweeps (Sec. IV.A uses n_or = 10; the
+ * benchmarked configurations use 4).  plaq_out (optional, n_sweeps doubles,
+ * host or device) receives the average plaquette after each compound sweep. */
+mgq_status mgq_update_sweeps(mgq_lattice* lat, double beta, uint64_t sweep0, int n_sweeps, int n_hb,
+                             int n_or, double* plaq_out, void* stream);
+
+/* ---- observables (Sec. III, IV.B-C) ----------------------------------------- */
+
+/* Average plaquette (1/(6V)) sum_x sum_{mu<nu} (1/3) Re Tr U_munu(x),
+ * accumulated in FP64.  plaq_out: one double, host or device. */
+mgq_status mgq_plaquette(const mgq_lattice* lat, double* plaq_out, void* stream);
+
+/* Clover energy density E = (1/V) sum_x -1/2 sum_{mu,nu} Tr G_munu^2 and
+ * charge Q = -1/(32 pi^2) sum_x eps_{munurhosigma} Tr G_munu G_rhosigma,
+ * G_munu = traceless part of (Q_munu - Q_munu^+)/8 (four clover leaves).
+ * E_out, Q_out: one double each (either may be NULL), host or device. */
+mgq_status mgq_topo_charge(const mgq_lattice* lat, double* E_out, double* Q_out, void* stream);
+
+/* Wilson flow with fixed step eps (Sec. IV.B), Luscher's third-order
+ * Runge-Kutta scheme with generator Z(W) = -TA(W A(W)); n_steps steps, the
+ * links are replaced by the flowed field.  E and Q (as mgq_topo_charge) are
+ * measured at t = k eps for k = 0, meas_every, 2 meas_every, ... <= n_steps:
+ * E_out, Q_out hold n_steps/meas_every + 1 doubles (host or device, NULL to
+ * skip).  Uses the workspace's algebra buffer.  Errors: MGQ_EINVAL, MGQ_ENOMEM. */
+mgq_status mgq_wilson_flow(mgq_lattice* lat, double eps, int n_steps, int meas_every, double* E_out,
+                           double* Q_out, void* stream);
+
+/* ---- HMC (Sec. IV.D, App. A) ------------------------------------------------- */
+
+/* Gauge force F(x,mu) = -(beta/6) TA(U_mu(x) A_mu(x)) into force_out
+ * (device, mom layout and precision); dP/dt = F for H = sum p^2/2 + S. */
+mgq_status mgq_hmc_force(const mgq_lattice* lat, double beta, void* force_out, void* stream);
+
+/* One unit-length-style trajectory of length tau with n_steps PQP leapfrog
+ * steps: Gaussian momenta from the momentum stream of `traj` into lat->mom,
+ * H0 = sum p^2/2 + S (FP64), P(e/2) [Q(e) P(e)]^(n-1) Q(e) P(e/2) with
+ * Q(e): U <- exp(e P) U, H1, dH = H1 - H0 (FP64); accept iff u < exp(-dH)
+ * with u from the accept stream of `traj`; accept_reject = 0 accepts
+ * unconditionally (warm-up trajectories, Sec. IV.E).  A rejection restores
+ * the links from the workspace copy.  dH_out / accepted_out: one double /
+ * one int, host or device, either may be NULL.  Needs lat->mom.
+ * Errors: MGQ_EINVAL, MGQ_ENOMEM. */
+mgq_status mgq_hmc_trajectory(mgq_lattice* lat, double beta, double tau, int n_steps, uint64_t traj,
+                              int accept_reject, double* dH_out, int* accepted_out, void* stream);
+
+/* ---- multiscale maps (Sec. III: Eqs. restriction, prolongation, smoothing,
+ *      APE) ------------------------------------------------------------------ */
+
+/* Prolongation of `coarse` onto `fine` (fine dims = 2 x coarse dims, same
+ * precision): transfer U^f_mu(n) = U^c_mu(n/2), U^f_mu(n+e_mu) = 1 at chi(n)
+ * = 0 and 1 elsewhere; then for d = 0, 1, 2 Jacobi APE steps
+ * U <- P_SU(3)[U + c sum_{nu: n_nu odd} (T+ + T-)] on the bonds with
+ * chi_mu(n) = d + 1 until |S_d(k) - S_d(k-1)| <= rel_tol |S_d(k-1)| or
+ * max_iter steps (rel_tol <= 0: exactly max_iter steps).  iters_out (host,
+ * 3 ints) and sd_out (host, 3 doubles, optional) receive the steps taken and
+ * the final S_d / beta.  Uses fine->work.  Errors: MGQ_EINVAL, MGQ_ENOMEM. */
+mgq_status mgq_prolongate(const mgq_lattice* coarse, mgq_lattice* fine, double c, double rel_tol,
+                          int max_iter, int* iters_out, double* sd_out, void* stream);
+
+/* Restriction U^c_mu(n/2) = U^f_mu(n) U^f_mu(n + e_mu) at chi(n) = 0. */
+mgq_status mgq_restrict(const mgq_lattice* fine, mgq_lattice* coarse, void* stream);
+
+/* ---- checks ------------------------------------------------------------------ */
+/* max over links of max(|U U^+ - 1|, |det U - 1|) into max_dev_out (one
+ * HOST double, may be NULL); synchronises `stream`.  Returns MGQ_ENONUNITARY
+ * when the deviation exceeds tol (> 0).  Uses the workspace. */
+mgq_status mgq_check_unitarity(const mgq_lattice* lat, double tol, double* max_dev_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGQ_H */

@@ -58,6 +58,7 @@ _SIGS = {
     "orc_heatbath_one_link": (None, [_D, _I, _dbl, _u64, _u32, _u64, _int, _long, _int, _D, _U8]),
     "orc_overrelax_sweep": (None, [_D, _I]),
     "orc_overrelax_one_link": (None, [_D, _I, _long, _int, _D]),
+    "orc_overrelax_subsweep": (None, [_D, _I, _int, _int]),
     "orc_update_chain": (None, [_D, _I, _dbl, _u64, _u32, _u64, _int, _int, _int, _D]),
     "orc_expm": (None, [_D, _D]),
     "orc_alg_to_mat": (None, [_D, _D]),
@@ -220,6 +221,10 @@ def heatbath_one_link(U, dims, beta, seed, lattice_id, sweep, n_hb, s, mu):
 
 def overrelax_sweep(U, dims):
     lib().orc_overrelax_sweep(_dp(U.view(np.float64)), _dims(dims))
+
+
+def overrelax_subsweep(U, dims, mu, parity):
+    lib().orc_overrelax_subsweep(_dp(U.view(np.float64)), _dims(dims), int(mu), int(parity))
 
 
 def overrelax_one_link(U, dims, s, mu):

@@ -614,6 +614,18 @@ void orc_overrelax_sweep(double* U, const int* dims)
         }
 }
 
+/* One (mu, parity) subset of the overrelaxation sweep. */
+void orc_overrelax_subsweep(double* U, const int* dims, int mu, int par)
+{
+    lat_t g = make_lat(dims);
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < g.V; s++) {
+        if (parity_of(&g, s) != par) continue;
+        mat3 A = staple(&g, U, s, mu);
+        setU(U, s, mu, or_link(getU(U, s, mu), A));
+    }
+}
+
 /* The overrelaxation result for a single link, without modifying U. */
 void orc_overrelax_one_link(const double* U, const int* dims, long s, int mu, double* Uout)
 {

@@ -1,0 +1,219 @@
+"""Python face of libmgq: the same entry points as include/mgq.h, taking a
+:class:`Lattice` whose device buffers are torch tensors.  Only argument
+marshalling happens here; every step of the hot path runs in the CUDA
+kernels of libmgq."""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import MGQ_F32, MGQ_F32_C12, MGQ_F64, MgqError, MgqLattice, call
+
+PRECISIONS = {"f64": MGQ_F64, "f32": MGQ_F32, "f32c12": MGQ_F32_C12}
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Lattice:
+    """One lattice: extents, precision, RNG key and its device buffers.
+
+    links / work (and mom, when ``with_mom``) are uint8 torch tensors of the
+    sizes the library asks for; the struct handed to the C ABI points into
+    them.
+    """
+
+    def __init__(self, dims: Sequence[int], prec: str = "f64", seed: int = 0, lattice_id: int = 0,
+                 with_mom: bool = False, device: str | torch.device = "cuda"):
+        self.dims = [int(v) for v in dims]
+        self.prec = prec
+        self.device = torch.device(device)
+        c = MgqLattice()
+        for m in range(4):
+            c.dims[m] = self.dims[m]
+            c.bc[m] = 0
+        c.prec = PRECISIONS[prec]
+        c.action = 0
+        c.seed = int(seed)
+        c.lattice_id = int(lattice_id)
+        c.reserved = 0
+        L = _lib.load()
+        nl = int(L.mgq_links_bytes(ctypes.byref(c)))
+        if nl == 0:
+            raise MgqError(_lib.MGQ_EINVAL, f"invalid extents {self.dims} for prec {prec}")
+        nw = int(L.mgq_workspace_bytes(ctypes.byref(c)))
+        nm = int(L.mgq_mom_bytes(ctypes.byref(c)))
+        self.links = torch.zeros(nl, dtype=torch.uint8, device=self.device)
+        self.work = torch.zeros(nw, dtype=torch.uint8, device=self.device)
+        self.mom = torch.zeros(nm, dtype=torch.uint8, device=self.device) if with_mom else None
+        c.links = self.links.data_ptr()
+        c.work = self.work.data_ptr()
+        c.work_bytes = nw
+        c.mom = self.mom.data_ptr() if self.mom is not None else None
+        self.c = c
+        self.volume = int(np.prod(self.dims))
+        self.site_stride = int(L.mgq_site_stride((ctypes.c_int32 * 4)(*self.dims)))
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.c)
+
+    @property
+    def seed(self) -> int:
+        return int(self.c.seed)
+
+    @property
+    def lattice_id(self) -> int:
+        return int(self.c.lattice_id)
+
+    def real_dtype(self) -> torch.dtype:
+        return torch.float64 if self.prec == "f64" else torch.float32
+
+    def new_alg_field(self) -> torch.Tensor:
+        """A zeroed device buffer in the momentum layout (4*2*8*S reals)."""
+        return torch.zeros(4 * 2 * 8 * self.site_stride, dtype=self.real_dtype(), device=self.device)
+
+    # ---------------------------------------------------------- canonical I/O
+    def to_numpy(self, stream=None) -> np.ndarray:
+        """Export the links as complex128 (V, 4, 3, 3) in lexicographic site order."""
+        buf = torch.empty(self.volume * 72, dtype=torch.float64, device=self.device)
+        mgq_export_links(self, buf, stream)
+        return buf.cpu().numpy().view(np.complex128).reshape(self.volume, 4, 3, 3)
+
+    def from_numpy(self, U: np.ndarray, stream=None) -> None:
+        """Import links given as complex128 (V, 4, 3, 3) in lexicographic site order."""
+        a = np.ascontiguousarray(U, dtype=np.complex128).view(np.float64).reshape(-1)
+        buf = torch.from_numpy(a.copy()).to(self.device)
+        mgq_import_links(self, buf, stream)
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+
+    def mom_numpy(self) -> np.ndarray:
+        """Momenta as float64 (V, 4, 8) in lexicographic site order."""
+        return alg_to_numpy(self, self.mom)
+
+
+def alg_to_numpy(lat: Lattice, buf: torch.Tensor) -> np.ndarray:
+    """A buffer in the momentum layout, as float64 (V, 4, 8) in lexicographic site order."""
+    S = lat.site_stride
+    a = buf.view(lat.real_dtype()).reshape(4, 2, 8, S)[..., : lat.volume // 2].double().cpu().numpy()
+    L = lat.dims
+    idx = np.arange(lat.volume)
+    x = [(idx // int(np.prod(L[:m]))) % L[m] for m in range(4)]
+    par = (x[0] + x[1] + x[2] + x[3]) % 2
+    h = idx // 2
+    out = np.empty((lat.volume, 4, 8))
+    for mu in range(4):
+        out[:, mu, :] = a[mu, par, :, h]
+    return out
+
+
+# ------------------------------------------------------------------ entry points
+def mgq_init_links(lat: Lattice, start: int, stream=None) -> None:
+    call("mgq_init_links", lat.ref, int(start), _stream_handle(stream))
+
+
+def mgq_import_links(lat: Lattice, canon: torch.Tensor, stream=None) -> None:
+    call("mgq_import_links", lat.ref, _ptr(canon), _stream_handle(stream))
+
+
+def mgq_export_links(lat: Lattice, canon: torch.Tensor, stream=None) -> None:
+    call("mgq_export_links", lat.ref, _ptr(canon), _stream_handle(stream))
+
+
+def mgq_heatbath_sweep(lat: Lattice, beta: float, sweep: int, n_hb: int = 1, stream=None) -> None:
+    call("mgq_heatbath_sweep", lat.ref, float(beta), int(sweep), int(n_hb), _stream_handle(stream))
+
+
+def mgq_heatbath_subsweep(lat: Lattice, beta: float, sweep: int, n_hb: int, mu: int, parity: int,
+                          decisions: Optional[torch.Tensor] = None, stream=None) -> None:
+    call("mgq_heatbath_subsweep", lat.ref, float(beta), int(sweep), int(n_hb), int(mu), int(parity),
+         _ptr(decisions), _stream_handle(stream))
+
+
+def mgq_overrelax_sweep(lat: Lattice, stream=None) -> None:
+    call("mgq_overrelax_sweep", lat.ref, _stream_handle(stream))
+
+
+def mgq_update_sweeps(lat: Lattice, beta: float, sweep0: int, n_sweeps: int, n_hb: int = 1, n_or: int = 4,
+                      plaq_out=None, stream=None):
+    """n_sweeps x (1 HB + n_or OR); returns the per-sweep plaquettes when plaq_out is True or a tensor."""
+    out = None
+    if plaq_out is True:
+        out = np.zeros(n_sweeps)
+        ptr = ctypes.c_void_p(out.ctypes.data)
+    elif isinstance(plaq_out, torch.Tensor):
+        ptr = _ptr(plaq_out)
+    elif isinstance(plaq_out, np.ndarray):
+        out = plaq_out
+        ptr = ctypes.c_void_p(plaq_out.ctypes.data)
+    else:
+        ptr = None
+    call("mgq_update_sweeps", lat.ref, float(beta), int(sweep0), int(n_sweeps), int(n_hb), int(n_or), ptr,
+         _stream_handle(stream))
+    return out
+
+
+def mgq_plaquette(lat: Lattice, out=None, stream=None) -> Optional[float]:
+    """Average plaquette; into `out` (device tensor) or returned as a float."""
+    if out is not None:
+        call("mgq_plaquette", lat.ref, _ptr(out), _stream_handle(stream))
+        return None
+    v = ctypes.c_double()
+    call("mgq_plaquette", lat.ref, ctypes.byref(v), _stream_handle(stream))
+    return float(v.value)
+
+
+def mgq_topo_charge(lat: Lattice, stream=None):
+    E, Q = ctypes.c_double(), ctypes.c_double()
+    call("mgq_topo_charge", lat.ref, ctypes.byref(E), ctypes.byref(Q), _stream_handle(stream))
+    return float(E.value), float(Q.value)
+
+
+def mgq_wilson_flow(lat: Lattice, eps: float, n_steps: int, meas_every: int, stream=None):
+    m = n_steps // meas_every + 1
+    E, Q = np.zeros(m), np.zeros(m)
+    call("mgq_wilson_flow", lat.ref, float(eps), int(n_steps), int(meas_every), ctypes.c_void_p(E.ctypes.data),
+         ctypes.c_void_p(Q.ctypes.data), _stream_handle(stream))
+    return E, Q
+
+
+def mgq_hmc_force(lat: Lattice, beta: float, force_out: torch.Tensor, stream=None) -> None:
+    call("mgq_hmc_force", lat.ref, float(beta), _ptr(force_out), _stream_handle(stream))
+
+
+def mgq_hmc_trajectory(lat: Lattice, beta: float, tau: float, n_steps: int, traj: int, accept_reject: int = 1,
+                       stream=None):
+    dH, acc = ctypes.c_double(), ctypes.c_int()
+    call("mgq_hmc_trajectory", lat.ref, float(beta), float(tau), int(n_steps), int(traj), int(accept_reject),
+         ctypes.byref(dH), ctypes.byref(acc), _stream_handle(stream))
+    return float(dH.value), int(acc.value)
+
+
+def mgq_prolongate(coarse: Lattice, fine: Lattice, c: float = 0.05, rel_tol: float = 1e-5, max_iter: int = 10000,
+                   stream=None):
+    iters = (ctypes.c_int * 3)()
+    sd = (ctypes.c_double * 3)()
+    call("mgq_prolongate", coarse.ref, fine.ref, float(c), float(rel_tol), int(max_iter), iters, sd,
+         _stream_handle(stream))
+    return [int(v) for v in iters], [float(v) for v in sd]
+
+
+def mgq_restrict(fine: Lattice, coarse: Lattice, stream=None) -> None:
+    call("mgq_restrict", fine.ref, coarse.ref, _stream_handle(stream))
+
+
+def mgq_check_unitarity(lat: Lattice, tol: float = 0.0, stream=None) -> float:
+    v = ctypes.c_double()
+    call("mgq_check_unitarity", lat.ref, float(tol), ctypes.byref(v), _stream_handle(stream))
+    return float(v.value)

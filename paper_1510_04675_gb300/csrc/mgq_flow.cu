@@ -1,0 +1,144 @@
+// libmgq Wilson flow (Sec. IV.B; fixed step, Luscher's third-order
+// Runge-Kutta integrator) and clover observables E(t), Q(t) (Sec. IV.B-C).
+#include "mgq_internal.h"
+#include "mgq_stencil.cuh"
+
+namespace mgq {
+
+mgq_status force_accumulate(const mgq_lattice* lat, void* B, double coef, double alpha, cudaStream_t st);
+mgq_status exp_update(const mgq_lattice* lat, void* B, double s, cudaStream_t st);
+
+// Clover leaves around x in the (mu,nu) plane, all starting and ending at x,
+// counterclockwise; returns the algebra coefficients g of
+// G = traceless part of (Q - Q^+)/8, i.e. g = t(TA(Q))/4.
+template <class T, int NP>
+__device__ __forceinline__ void clover_coeffs(const Links<T, NP>& U, const Geom& g, const int x[4], int par, int h, int mu,
+                                              int nu, T out[8]) {
+    const int op = par ^ 1;
+    const int lpm = lex_hop(g, x, mu, +1), lpn = lex_hop(g, x, nu, +1);
+    const int lmm = lex_hop(g, x, mu, -1), lmn = lex_hop(g, x, nu, -1);
+    const int lmm_pn = lex_hop(g, x, mu, -1, nu, +1);
+    const int lmm_mn = lex_hop(g, x, mu, -1, nu, -1);
+    const int lpm_mn = lex_hop(g, x, mu, +1, nu, -1);
+    const M3<T> umu = U.load(mu, par, h), unu = U.load(nu, par, h);
+    // l1 = U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
+    M3<T> Q = mul_nd(mul_nn(umu, U.load(nu, op, lpm >> 1)), mul_nn(unu, U.load(mu, op, lpn >> 1)));
+    // l2 = U_nu(x) U_mu(x-mu+nu)^+ U_nu(x-mu)^+ U_mu(x-mu)
+    {
+        const M3<T> a = U.load(mu, par, lmm_pn >> 1), b = U.load(nu, op, lmm >> 1), c = U.load(mu, op, lmm >> 1);
+        acc_add(Q, mul_nn(mul_nd(unu, a), mul_dn(b, c)));
+    }
+    // l3 = U_mu(x-mu)^+ U_nu(x-mu-nu)^+ U_mu(x-mu-nu) U_nu(x-nu)
+    {
+        const M3<T> a = U.load(mu, op, lmm >> 1), b = U.load(nu, par, lmm_mn >> 1), c = U.load(mu, par, lmm_mn >> 1),
+                    d = U.load(nu, op, lmn >> 1);
+        acc_add(Q, mul_nn(mul_dd(a, b), mul_nn(c, d)));
+    }
+    // l4 = U_nu(x-nu)^+ U_mu(x-nu) U_nu(x+mu-nu) U_mu(x)^+
+    {
+        const M3<T> a = U.load(nu, op, lmn >> 1), b = U.load(mu, op, lmn >> 1), c = U.load(nu, par, lpm_mn >> 1);
+        acc_add(Q, mul_nd(mul_nn(mul_dn(a, b), c), umu));
+    }
+    ta_coeffs(Q, out);
+#pragma unroll
+    for (int a = 0; a < 8; a++) out[a] *= T(0.25);
+}
+
+// Per site: E(x) = -1/2 sum_{mu,nu} Tr G^2 = 1/2 sum_{mu<nu} |g_munu|^2 and
+// q(x) = -1/(32 pi^2) eps Tr(G G) = 1/(8 pi^2) (g01.g23 - g02.g13 + g03.g12),
+// using Tr(X_a X_b) = -delta_ab / 2.
+template <class T, int NP>
+__global__ void __launch_bounds__(128) k_clover(Links<T, NP> U, Geom g, double* __restrict__ partials) {
+    double e = 0.0, q = 0.0;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.V; idx += gridDim.x * blockDim.x) {
+        const int par = idx >= g.Vh, h = idx - par * g.Vh;
+        int x[4];
+        cb_coords(g, par, h, x);
+        T G[6][8];
+        const int pl[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+#pragma unroll 1
+        for (int p = 0; p < 6; p++) clover_coeffs(U, g, x, par, h, pl[p][0], pl[p][1], G[p]);
+        double es = 0.0, d01_23 = 0.0, d02_13 = 0.0, d03_12 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 8; a++) {
+#pragma unroll
+            for (int p = 0; p < 6; p++) es += (double)G[p][a] * (double)G[p][a];
+            d01_23 += (double)G[0][a] * (double)G[5][a];
+            d02_13 += (double)G[1][a] * (double)G[4][a];
+            d03_12 += (double)G[2][a] * (double)G[3][a];
+        }
+        e += 0.5 * es;
+        q += (d01_23 - d02_13 + d03_12) * (1.0 / (8.0 * 9.869604401089358));
+    }
+    e = block_sum(e);
+    q = block_sum(q);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = e;
+        partials[gridDim.x + blockIdx.x] = q;
+    }
+}
+
+mgq_status clover_into(const mgq_lattice* lat, double* partials, double* dev_out, cudaStream_t st) {
+    const Geom g = make_geom(lat->dims);
+    const int nb = reduction_blocks(g.V, 128) < 2048 ? reduction_blocks(g.V, 128) : 2048;
+    dispatch_prec(lat->prec, [&]<class T, int NP>() {
+        k_clover<T, NP><<<nb, 128, 0, st>>>(links_of<T, NP>(lat), g, partials);
+    });
+    launch_final_sum(partials, nb, 1.0 / (double)g.V, dev_out, st);
+    launch_final_sum(partials + nb, nb, 1.0, dev_out + 1, st);
+    return cuda_check("clover");
+}
+
+}  // namespace mgq
+
+using namespace mgq;
+
+extern "C" {
+
+mgq_status mgq_topo_charge(const mgq_lattice* lat, double* E_out, double* Q_out, void* stream) {
+    mgq_status s = check_lattice(lat, true, "mgq_topo_charge");
+    if (s) return s;
+    cudaStream_t st = as_stream(stream);
+    double* sc = ws_scalars(lat);
+    if ((s = clover_into(lat, ws_partials(lat), sc + 16, st))) return s;
+    if ((s = deliver(sc + 16, E_out, E_out ? 1 : 0, st, "mgq_topo_charge"))) return s;
+    return deliver(sc + 17, Q_out, Q_out ? 1 : 0, st, "mgq_topo_charge");
+}
+
+mgq_status mgq_wilson_flow(mgq_lattice* lat, double eps, int n_steps, int meas_every, double* E_out, double* Q_out,
+                           void* stream) {
+    mgq_status s = check_lattice(lat, true, "mgq_wilson_flow");
+    if (s) return s;
+    if (!(eps > 0.0) || n_steps < 0 || meas_every < 1)
+        return fail(MGQ_EINVAL, "mgq_wilson_flow: need eps > 0, n_steps >= 0, meas_every >= 1");
+    const int nm = n_steps / meas_every + 1;
+    if (2 * nm + 32 > (int)WS_NSCALARS) return fail(MGQ_EINVAL, "mgq_wilson_flow: at most %d measurements", (int)(WS_NSCALARS - 32) / 2);
+    cudaStream_t st = as_stream(stream);
+    double* sc = ws_scalars(lat);
+    double* meas = sc + 32;  // E at meas[2m], Q at meas[2m+1]
+    void* B = ws_alg(lat);
+    int m = 0;
+    for (int k = 0; k <= n_steps; k++) {
+        if (k % meas_every == 0) {
+            if ((s = clover_into(lat, ws_partials(lat), meas + 2 * m, st))) return s;
+            m++;
+        }
+        if (k == n_steps) break;
+        // Z_i = eps Z(W_i), Z(W) = -TA(W A(W)):
+        // W1 = exp(Z0/4) W0; W2 = exp(8/9 Z1 - 17/36 Z0) W1; W3 = exp(3/4 Z2 - 8/9 Z1 + 17/36 Z0) W2
+        if ((s = force_accumulate(lat, B, -eps, 0.0, st))) return s;              // B = Z0
+        if ((s = exp_update(lat, B, 0.25, st))) return s;
+        if ((s = force_accumulate(lat, B, -eps * 8.0 / 9.0, -17.0 / 36.0, st))) return s;  // B = 8/9 Z1 - 17/36 Z0
+        if ((s = exp_update(lat, B, 1.0, st))) return s;
+        if ((s = force_accumulate(lat, B, -eps * 0.75, -1.0, st))) return s;       // B = 3/4 Z2 - B
+        if ((s = exp_update(lat, B, 1.0, st))) return s;
+    }
+    // gather strided E, Q pairs
+    for (int i = 0; i < nm; i++) {
+        if (E_out && (s = deliver(meas + 2 * i, E_out + i, 1, st, "mgq_wilson_flow"))) return s;
+        if (Q_out && (s = deliver(meas + 2 * i + 1, Q_out + i, 1, st, "mgq_wilson_flow"))) return s;
+    }
+    return MGQ_OK;
+}
+
+}  // extern "C"

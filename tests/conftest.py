@@ -20,3 +20,22 @@ def orc():
     oracle.build()
     oracle.lib()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def mgqlib():
+    """The built libmgq (compiled in-tree if missing or stale)."""
+    from paper_1510_04675_gb300 import _lib, build
+
+    build.build()
+    return _lib.load()
+
+
+@pytest.fixture(scope="session")
+def gpu(mgqlib):
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1510_04675_gb300 import api
+
+    return api
