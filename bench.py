@@ -178,7 +178,7 @@ def traffic_from_profiles(kernel: str, workload_tag: str):
     for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.txt"))):
         for line in open(f):
             t = line.split()
-            if len(t) >= 7 and t[0] == "traffic_bytes_per_launch" and t[1] == kernel and t[2] == workload_tag \
+            if len(t) >= 6 and t[0] == "traffic_bytes_per_launch" and t[1] == kernel and t[2] == workload_tag \
                     and t[4] == "src_hash":
                 if t[5] == cur:
                     return float(t[3])
