@@ -147,6 +147,24 @@ mgq_status mgq_update_sweeps(mgq_lattice* lat, double beta, uint64_t sweep0, int
  * accumulated in FP64.  plaq_out: one double, host or device. */
 mgq_status mgq_plaquette(const mgq_lattice* lat, double* plaq_out, void* stream);
 
+/* The same average plaquette for callers that cannot give the library any
+ * device memory (for example code running under another framework's memory
+ * manager that owns the device memory and forbids further cudaMalloc, or a
+ * latency-critical monitoring hook where cudaMalloc/cudaFree would implicitly
+ * synchronise the device).  The paper has no counterpart: this is a library
+ * convenience.  It ignores lat->work and allocates nothing; its scratch is a
+ * fixed 64 KiB static device array inside libmgq that every GPU loading the
+ * library holds until exit.  Limit: V <= 2,096,896 sites (one partial sum per
+ * 256 sites, 8191 slots; e.g. 32^4 fits, 48^4 does not); larger lattices get
+ * MGQ_EINVAL and should use mgq_plaquette.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array and it keeps the last call's contents (each call rewrites
+ * every slot it reads), so calls that overlap on the GPU -- concurrent
+ * streams, or other host threads on the same device -- race and must be
+ * serialised by the caller.  plaq_out: one double, host or device. */
+mgq_status mgq_plaquette_noalloc(const mgq_lattice* lat, double* plaq_out, void* stream);
+
 /* Clover energy density E = (1/V) sum_x -1/2 sum_{mu,nu} Tr G_munu^2 and
  * charge Q = -1/(32 pi^2) sum_x eps_{munurhosigma} Tr G_munu G_rhosigma,
  * G_munu = traceless part of (Q_munu - Q_munu^+)/8 (four clover leaves).

@@ -58,6 +58,7 @@ SIGNATURES = {
     "mgq_overrelax_sweep": (_st, [_P, _vp]),
     "mgq_update_sweeps": (_st, [_P, _d, _u64, _i, _i, _i, _vp, _vp]),
     "mgq_plaquette": (_st, [_P, _vp, _vp]),
+    "mgq_plaquette_noalloc": (_st, [_P, _vp, _vp]),
     "mgq_topo_charge": (_st, [_P, _vp, _vp, _vp]),
     "mgq_wilson_flow": (_st, [_P, _d, _i, _i, _vp, _vp, _vp]),
     "mgq_hmc_force": (_st, [_P, _d, _vp, _vp]),
