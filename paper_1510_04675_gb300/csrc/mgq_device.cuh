@@ -114,6 +114,111 @@ template <class T> __device__ __forceinline__ M3<T> mul_dd(const M3<T>& a, const
             r.e[i][j] = conjg(b.e[j][0] * a.e[0][i] + b.e[j][1] * a.e[1][i] + b.e[j][2] * a.e[2][i]);
     return r;
 }
+// FP32 products on the packed f32x2 FMA of sm_100+: a complex product is
+// a.re * (b.re, b.im) + a.im * (-b.im, b.re), two paired FMAs instead of four.
+__device__ __forceinline__ float2 bcast(float x) { return make_float2(x, x); }
+__device__ __forceinline__ Cx<float> from_f2(float2 z) { return mk(z.x, z.y); }
+
+template <> __device__ __forceinline__ M3<float> mul_nn<float>(const M3<float>& a, const M3<float>& b) {
+    float2 B[3][3], iB[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            B[k][j] = make_float2(b.e[k][j].re, b.e[k][j].im);
+            iB[k][j] = make_float2(-b.e[k][j].im, b.e[k][j].re);
+        }
+    M3<float> r;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                acc = __ffma2_rn(bcast(a.e[i][k].re), B[k][j], acc);
+                acc = __ffma2_rn(bcast(a.e[i][k].im), iB[k][j], acc);
+            }
+            r.e[i][j] = from_f2(acc);
+        }
+    return r;
+}
+// a b^+ : sum_k a_ik conj(b_jk) = a.re * conj(b) + a.im * (b.im, b.re)
+template <> __device__ __forceinline__ M3<float> mul_nd<float>(const M3<float>& a, const M3<float>& b) {
+    float2 C[3][3], iC[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; j++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            C[j][k] = make_float2(b.e[j][k].re, -b.e[j][k].im);
+            iC[j][k] = make_float2(b.e[j][k].im, b.e[j][k].re);
+        }
+    M3<float> r;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                acc = __ffma2_rn(bcast(a.e[i][k].re), C[j][k], acc);
+                acc = __ffma2_rn(bcast(a.e[i][k].im), iC[j][k], acc);
+            }
+            r.e[i][j] = from_f2(acc);
+        }
+    return r;
+}
+// a^+ b : sum_k conj(a_ki) b_kj = a.re * b - a.im * (-b.im, b.re)
+template <> __device__ __forceinline__ M3<float> mul_dn<float>(const M3<float>& a, const M3<float>& b) {
+    float2 B[3][3], iB[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            B[k][j] = make_float2(b.e[k][j].re, b.e[k][j].im);
+            iB[k][j] = make_float2(-b.e[k][j].im, b.e[k][j].re);
+        }
+    M3<float> r;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                acc = __ffma2_rn(bcast(a.e[k][i].re), B[k][j], acc);
+                acc = __ffma2_rn(bcast(-a.e[k][i].im), iB[k][j], acc);
+            }
+            r.e[i][j] = from_f2(acc);
+        }
+    return r;
+}
+// a^+ b^+ : sum_k conj(a_ki) conj(b_jk) = a.re * conj(b) - a.im * (b.im, b.re)
+template <> __device__ __forceinline__ M3<float> mul_dd<float>(const M3<float>& a, const M3<float>& b) {
+    float2 C[3][3], iC[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; j++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            C[j][k] = make_float2(b.e[j][k].re, -b.e[j][k].im);
+            iC[j][k] = make_float2(b.e[j][k].im, b.e[j][k].re);
+        }
+    M3<float> r;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                acc = __ffma2_rn(bcast(a.e[k][i].re), C[j][k], acc);
+                acc = __ffma2_rn(bcast(-a.e[k][i].im), iC[j][k], acc);
+            }
+            r.e[i][j] = from_f2(acc);
+        }
+    return r;
+}
+
 template <class T> __device__ __forceinline__ void acc_add(M3<T>& a, const M3<T>& b) {
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -198,10 +303,12 @@ __device__ __forceinline__ int lex_of(const Geom& g, const int x[4]) {
 __device__ __forceinline__ int wrap(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
 
 // Lexicographic index of x + dmu e_mu + dnu e_nu (|d| <= 1, periodic).
+// Written with compile-time array indices only, so that a run-time mu or nu
+// does not push the coordinates into local memory.
 __device__ __forceinline__ int lex_hop(const Geom& g, const int x[4], int mu, int dmu, int nu = 0, int dnu = 0) {
-    int y[4] = {x[0], x[1], x[2], x[3]};
-    y[mu] = wrap(y[mu] + dmu, g.L[mu]);
-    y[nu] = wrap(y[nu] + dnu, g.L[nu]);
+    int y[4];
+#pragma unroll
+    for (int d = 0; d < 4; d++) y[d] = wrap(x[d] + (d == mu ? dmu : 0) + (d == nu ? dnu : 0), g.L[d]);
     return lex_of(g, y);
 }
 

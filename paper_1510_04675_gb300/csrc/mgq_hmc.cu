@@ -9,12 +9,16 @@
 namespace mgq {
 
 // B <- alpha B + coef t(TA(U A)), t the algebra coefficients of TA(U A);
-// alpha == 0 writes without reading B.
+// alpha == 0 writes without reading B.  A block of 8 warps covers 32
+// consecutive sites in all eight (mu, parity) planes (warp w: mu = w/2,
+// parity = w%2), so the neighbour links of a site band are used by all
+// directions while they are still in cache.
 template <class T, int NP>
-__global__ void __launch_bounds__(128) k_force(Links<T, NP> U, Geom g, Alg<T> B, T coef, T alpha) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= 8 * g.Vh) return;
-    const int mp = idx / g.Vh, h = idx - mp * g.Vh, mu = mp >> 1, par = mp & 1;
+__global__ void __launch_bounds__(256, 2) k_force(Links<T, NP> U, Geom g, Alg<T> B, T coef, T alpha) {
+    const int w = threadIdx.x >> 5;
+    const int mu = w >> 1, par = w & 1;
+    const int h = blockIdx.x * 32 + (threadIdx.x & 31);
+    if (h >= g.Vh) return;
     int x[4];
     cb_coords(g, par, h, x);
     const M3<T> A = staple(U, g, x, h, mu, par);
@@ -123,7 +127,7 @@ static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 mgq_status force_accumulate(const mgq_lattice* lat, void* B, double coef, double alpha, cudaStream_t st) {
     const Geom g = make_geom(lat->dims);
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
-        k_force<T, NP><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(links_of<T, NP>(lat), g, alg_at<T>(B, lat->dims), (T)coef,
+        k_force<T, NP><<<nblk(g.Vh, 32), 256, 0, st>>>(links_of<T, NP>(lat), g, alg_at<T>(B, lat->dims), (T)coef,
                                                              (T)alpha);
     });
     return cuda_check("force");
