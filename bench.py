@@ -277,6 +277,52 @@ def time_sweeps(api, lat, beta, n_or, steps, sweep0):
     return (1 + n_or) * 4 * lat.volume * steps / (a.elapsed_time(b) * 1e-3)
 
 
+def batched_leg(api, beta_lo=5.8, beta_hi=6.1, n_sweeps=20, n_or=4, seed=4242):
+    """256 fine lattices (96 x 12^4, 96 x 16^4, 64 x 8^3x16, FP32 12-real) prolongated
+    from coarse lattices thermalised at beta in [5.8, 6.1]; n_sweeps compound sweeps
+    of all of them with per-lattice FP64 plaquettes, replayed from one CUDA graph."""
+    import numpy as np
+    import torch
+
+    rng = np.random.default_rng(seed)
+    shapes = [[12] * 4] * 96 + [[16] * 4] * 96 + [[8, 8, 8, 16]] * 64
+    betas = rng.uniform(beta_lo, beta_hi, size=len(shapes)).tolist()
+    coarse = [api.Lattice([d // 2 for d in s], "f32c12", seed=seed, lattice_id=i) for i, s in enumerate(shapes)]
+    for c in coarse:
+        api.mgq_init_links(c, 1)
+    api.mgq_update_sweeps_batched(api.Batch(coarse, betas), 0, 30, 1, n_or)
+    fine = [api.Lattice(s, "f32c12", seed=seed + 1, lattice_id=i) for i, s in enumerate(shapes)]
+    for c, f in zip(coarse, fine):
+        api.mgq_prolongate(c, f, 0.05, 0.0, 10)  # fixed 10 APE steps per stage
+    del coarse
+    batch = api.Batch(fine, betas, max_sweeps=1)
+    P = batch.plaquette_buffer(1)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for i in range(2):
+            api.mgq_update_sweeps_batched(batch, i, 1, 1, n_or, P, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        api.mgq_update_sweeps_batched(batch, 2, 1, 1, n_or, P, stream=torch.cuda.current_stream())
+    g.replay()
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record()
+    for _ in range(n_sweeps):
+        g.replay()
+    b.record()
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) * 1e-3
+    V = sum(int(np.prod(x)) for x in shapes)
+    return {"lattices": len(shapes), "sites": V, "sweeps": n_sweeps,
+            "link_updates_per_s": (1 + n_or) * 4 * V * n_sweeps / sec, "ms_per_sweep": 1e3 * sec / n_sweeps,
+            "plaquette_mean": float(P.mean().item()), "graph": True,
+            "workload": "96x12^4 + 96x16^4 + 64x8^3x16, beta in [5.8, 6.1], prolongated (10 APE steps/stage), "
+                        "1 HB + 4 OR per sweep, FP32 12-real, per-lattice FP64 plaquette"}
+
+
 def run_mgq(args, dims, world, rank, local):
     import torch
 
@@ -419,6 +465,12 @@ def run_mgq(args, dims, world, rank, local):
             out[key + "_link_updates_per_s"] = r
             del l2
         out["speedup_vs_fp64"] = (value / world) / out["fp64_plain_link_updates_per_s"]
+        del lat, host_links
+        torch.cuda.empty_cache()
+        try:
+            out["batched"] = batched_leg(api)
+        except Exception as e:  # noqa: BLE001 - reported in the line
+            out["batched"] = {"error": str(e)[:200]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample(dims, beta)
     if rank == 0:

@@ -141,6 +141,27 @@ mgq_status mgq_overrelax_sweep(mgq_lattice* lat, void* stream);
 mgq_status mgq_update_sweeps(mgq_lattice* lat, double beta, uint64_t sweep0, int n_sweeps, int n_hb,
                              int n_or, double* plaq_out, void* stream);
 
+/* ---- batched driver (Sec. II: the N_s prolongated configurations are
+ *      rethermalised independently, "embarrassingly parallel") ------------- */
+
+/* Bytes of caller workspace `batch_work` needed by mgq_update_sweeps_batched
+ * for n_lat lattices and n_sweeps plaquette records; 0 on invalid extents. */
+uint64_t mgq_batch_workspace_bytes(const mgq_lattice* lats, int n_lat, int n_sweeps);
+
+/* mgq_update_sweeps for n_lat independent lattices at once: each may have its
+ * own extents, coupling betas[l] (host array), seed and lattice_id; all share
+ * one precision and the sweep indices sweep0 + i.  Every sub-sweep is one
+ * launch over all lattices (descriptors passed by value, at most 128 lattices
+ * per launch), so the call can be captured into a CUDA graph.  Results are
+ * bit-identical to n_lat separate mgq_update_sweeps calls.  plaq_out
+ * (optional, host or device, n_sweeps x n_lat doubles, sweep-major) receives
+ * every lattice's FP64 average plaquette after each compound sweep and then
+ * needs batch_work (device, 256-B aligned, >= mgq_batch_workspace_bytes).
+ * Errors: MGQ_EINVAL (mixed precision, bad beta, ...), MGQ_ENOMEM. */
+mgq_status mgq_update_sweeps_batched(mgq_lattice* lats, int n_lat, const double* betas, uint64_t sweep0,
+                                     int n_sweeps, int n_hb, int n_or, double* plaq_out, void* batch_work,
+                                     uint64_t batch_work_bytes, void* stream);
+
 /* ---- observables (Sec. III, IV.B-C) ----------------------------------------- */
 
 /* Average plaquette (1/(6V)) sum_x sum_{mu<nu} (1/3) Re Tr U_munu(x),

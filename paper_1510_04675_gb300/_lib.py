@@ -66,6 +66,9 @@ SIGNATURES = {
     "mgq_prolongate": (_st, [_P, _P, _d, _d, _i, _vp, _vp, _vp]),
     "mgq_restrict": (_st, [_P, _P, _vp]),
     "mgq_check_unitarity": (_st, [_P, _d, _vp, _vp]),
+    "mgq_batch_workspace_bytes": (ctypes.c_uint64, [_P, _i, _i]),
+    "mgq_update_sweeps_batched": (_st, [_P, _i, ctypes.POINTER(ctypes.c_double), _u64, _i, _i, _i, _vp, _vp, _u64,
+                                        _vp]),
 }
 
 _lib = None

@@ -217,3 +217,38 @@ def mgq_check_unitarity(lat: Lattice, tol: float = 0.0, stream=None) -> float:
     v = ctypes.c_double()
     call("mgq_check_unitarity", lat.ref, float(tol), ctypes.byref(v), _stream_handle(stream))
     return float(v.value)
+
+
+# ------------------------------------------------------------------ batched driver
+class Batch:
+    """Independent lattices advanced together by mgq_update_sweeps_batched.
+
+    The ctypes array of their descriptors and the batch workspace (sized for
+    ``max_sweeps`` plaquette records) are built once, so repeated calls (and
+    CUDA-graph capture of them) pass the same pointers.
+    """
+
+    def __init__(self, lattices: Sequence[Lattice], betas: Sequence[float], max_sweeps: int = 64):
+        if len(lattices) != len(betas) or not lattices:
+            raise ValueError("need one beta per lattice")
+        self.lattices = list(lattices)
+        self.n = len(self.lattices)
+        self.arr = (MgqLattice * self.n)(*[l.c for l in self.lattices])
+        self.betas = (ctypes.c_double * self.n)(*[float(b) for b in betas])
+        self.max_sweeps = int(max_sweeps)
+        nb = int(_lib.load().mgq_batch_workspace_bytes(self.arr, self.n, self.max_sweeps))
+        if nb == 0:
+            raise MgqError(_lib.MGQ_EINVAL, "invalid lattice extents in batch")
+        self.work = torch.zeros(nb, dtype=torch.uint8, device=self.lattices[0].device)
+
+    def plaquette_buffer(self, n_sweeps: int) -> torch.Tensor:
+        return torch.zeros((n_sweeps, self.n), dtype=torch.float64, device=self.lattices[0].device)
+
+
+def mgq_update_sweeps_batched(batch: Batch, sweep0: int, n_sweeps: int, n_hb: int = 1, n_or: int = 4,
+                              plaq_out: Optional[torch.Tensor] = None, stream=None) -> None:
+    """n_sweeps compound sweeps on every lattice of the batch; plaq_out: device (n_sweeps, n) float64 or None."""
+    if plaq_out is not None and n_sweeps > batch.max_sweeps:
+        raise ValueError("batch workspace sized for fewer sweeps")
+    call("mgq_update_sweeps_batched", batch.arr, batch.n, batch.betas, int(sweep0), int(n_sweeps), int(n_hb),
+         int(n_or), _ptr(plaq_out), _ptr(batch.work), int(batch.work.numel()), _stream_handle(stream))

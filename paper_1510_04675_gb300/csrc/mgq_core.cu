@@ -221,75 +221,6 @@ __global__ void k_export(Links<T, NP> U, Geom g, double* __restrict__ canon) {
         }
 }
 
-// =============================================================== heat bath
-// One link: V = U A; per subgroup (0,1), (0,2), (1,2): w from the block,
-// k = 2 beta |w| / 3, up to n_hb Creutz attempts
-//   a0 = 1 + log1p((1 - u0) expm1(-2k)) / k, accept iff u1^2 <= 1 - a0^2,
-// direction cos(theta) = 2 u2 - 1, phi = 2 pi u3; R = X (w/|w|), U <- R U,
-// V <- R V; reunitarise at the end.  dec[s] = accepted attempt or 255.
-template <class T>
-__device__ __forceinline__ void hb_link(M3<T>& u, const M3<T>& A, T beta, int n_hb, const RngKey& rk, uint32_t lex,
-                                        uint32_t mu, uint8_t* dec) {
-    M3<T> v = mul_nn(u, A);
-#pragma unroll
-    for (int s = 0; s < 3; s++) {
-        const int i = (s == 2) ? 1 : 0, j = (s == 0) ? 1 : 2;
-        T w[4];
-        block_w(v, i, j, w);
-        const T xi = m_sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
-        uint8_t d = 255;
-        if (xi >= tiny_norm<T>()) {
-            const T k = T(2) * beta * xi / T(3);
-            const T em = m_expm1(T(-2) * k);
-            for (int att = 0; att < n_hb; att++) {
-                const uint4 r = draw(rk, lex, mu, (uint32_t)s, (uint32_t)att, KIND_HB);
-                const T u0 = u01<T>(r.x), u1 = u01<T>(r.y), u2 = u01<T>(r.z), u3 = u01<T>(r.w);
-                const T a0 = T(1) + m_log1p((T(1) - u0) * em) / k;
-                const T rest = sub_rn(T(1), mul_rn(a0, a0));
-                if (mul_rn(u1, u1) <= rest) {
-                    const T rad = m_sqrt(rest);
-                    const T ct = T(2) * u2 - T(1);
-                    const T st = m_sqrt(sub_rn(T(1), mul_rn(ct, ct)));
-                    T sp, cp;
-                    m_sincospi(T(2) * u3, &sp, &cp);
-                    const T X[4] = {a0, rad * st * cp, rad * st * sp, rad * ct};
-                    const T inv = T(1) / xi;
-                    const T wh[4] = {w[0] * inv, w[1] * inv, w[2] * inv, w[3] * inv};
-                    T R[4];
-                    qmul(X, wh, R);
-                    left_su2(u, i, j, R);
-                    left_su2(v, i, j, R);
-                    d = (uint8_t)att;
-                    break;
-                }
-            }
-        }
-        if (dec) dec[s] = d;
-    }
-    reunitarize(u);
-}
-
-// Overrelaxation of one link: per subgroup R = (w/|w|)^2; reunitarise.
-template <class T>
-__device__ __forceinline__ void or_link(M3<T>& u, const M3<T>& A) {
-    M3<T> v = mul_nn(u, A);
-#pragma unroll
-    for (int s = 0; s < 3; s++) {
-        const int i = (s == 2) ? 1 : 0, j = (s == 0) ? 1 : 2;
-        T w[4];
-        block_w(v, i, j, w);
-        const T n2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + w[3] * w[3];
-        if (!(m_sqrt(n2) >= tiny_norm<T>())) continue;
-        const T inv2 = T(1) / n2;
-        // (w/|w|)^2 = (w0^2 - |w_vec|^2, 2 w0 w_vec) / |w|^2
-        const T R[4] = {(w[0] * w[0] - w[1] * w[1] - w[2] * w[2] - w[3] * w[3]) * inv2, T(2) * w[0] * w[1] * inv2,
-                        T(2) * w[0] * w[2] * inv2, T(2) * w[0] * w[3] * inv2};
-        left_su2(u, i, j, R);
-        left_su2(v, i, j, R);
-    }
-    reunitarize(u);
-}
-
 // One thread per link of the (MU, par) subset; MU is a template parameter so
 // that every neighbour index is resolved at compile time.  Four resident
 // blocks of 128 threads per SM (at most 128 registers) measured fastest.
@@ -317,17 +248,6 @@ __global__ void __launch_bounds__(128, 4) k_overrelax(Links<T, NP> U, Geom g, in
     M3<T> u = U.load(MU, par, h);
     or_link(u, A);
     U.store(MU, par, h, u);
-}
-
-// Calls f.template operator()<MU>() for a run-time direction mu.
-template <class F>
-inline void dispatch_mu(int mu, F&& f) {
-    switch (mu) {
-        case 0: f.template operator()<0>(); break;
-        case 1: f.template operator()<1>(); break;
-        case 2: f.template operator()<2>(); break;
-        default: f.template operator()<3>(); break;
-    }
 }
 
 // =============================================================== plaquette

@@ -95,6 +95,17 @@ inline void dispatch_prec(int prec, F&& f) {
     }
 }
 
+// Calls f.template operator()<MU>() for a run-time direction mu.
+template <class F>
+inline void dispatch_mu(int mu, F&& f) {
+    switch (mu) {
+        case 0: f.template operator()<0>(); break;
+        case 1: f.template operator()<1>(); break;
+        case 2: f.template operator()<2>(); break;
+        default: f.template operator()<3>(); break;
+    }
+}
+
 // Block-wide FP64 sum in a fixed order (warp shuffles then shared memory);
 // the result is valid in thread 0.
 __device__ __forceinline__ double block_sum(double v) {
