@@ -207,6 +207,12 @@ mgq_status mgq_wilson_flow(mgq_lattice* lat, double eps, int n_steps, int meas_e
  * (device, mom layout and precision); dP/dt = F for H = sum p^2/2 + S. */
 mgq_status mgq_hmc_force(const mgq_lattice* lat, double beta, void* force_out, void* stream);
 
+/* The Q-step of the leapfrog (Sec. IV.D): U_mu(x) <- exp(s P_mu(x)) U_mu(x)
+ * on every link, P = sum_a p_a X_a read from `alg` (device, mom layout and
+ * precision), exact SU(3) exponential (Cayley-Hamilton form of Morningstar
+ * and Peardon); FP32 formats are reunitarised.  Errors: MGQ_EINVAL. */
+mgq_status mgq_link_exp_update(mgq_lattice* lat, const void* alg, double s, void* stream);
+
 /* One unit-length-style trajectory of length tau with n_steps PQP leapfrog
  * steps: Gaussian momenta from the momentum stream of `traj` into lat->mom,
  * H0 = sum p^2/2 + S (FP64), P(e/2) [Q(e) P(e)]^(n-1) Q(e) P(e/2) with

@@ -252,3 +252,57 @@ def mgq_update_sweeps_batched(batch: Batch, sweep0: int, n_sweeps: int, n_hb: in
         raise ValueError("batch workspace sized for fewer sweeps")
     call("mgq_update_sweeps_batched", batch.arr, batch.n, batch.betas, int(sweep0), int(n_sweeps), int(n_hb),
          int(n_or), _ptr(plaq_out), _ptr(batch.work), int(batch.work.numel()), _stream_handle(stream))
+
+
+def mgq_link_exp_update(lat: Lattice, alg: torch.Tensor, s: float = 1.0, stream=None) -> None:
+    """U <- exp(s P) U on every link, P from an algebra field in the momentum layout."""
+    call("mgq_link_exp_update", lat.ref, _ptr(alg), float(s), _stream_handle(stream))
+
+
+def copy_lattice(lat: Lattice, with_mom: bool = False) -> Lattice:
+    """A new lattice with the same extents, precision, RNG key and a copy of the links."""
+    c = Lattice(lat.dims, lat.prec, seed=lat.seed, lattice_id=lat.lattice_id, with_mom=with_mom, device=lat.device)
+    c.links.copy_(lat.links)
+    return c
+
+
+# ------------------------------------------------------------------ checkpoints
+_MAGIC = b"MGQCKPT1"
+
+
+def save_checkpoint(lat: Lattice, path: str, beta: float, sweep: int) -> None:
+    """Raw little-endian dump of the link buffer with a header (extents, precision,
+    seed, lattice id, beta, next sweep index) and a CRC-32 of the payload.  The
+    RNG is counter-based, so continuing from `sweep` reproduces the
+    uninterrupted chain bit for bit."""
+    import struct
+    import zlib
+
+    torch.cuda.synchronize()
+    payload = lat.links.cpu().numpy().tobytes()
+    hdr = struct.pack("<8s4iiQIdQQI", _MAGIC, *lat.dims, PRECISIONS[lat.prec], lat.seed, lat.lattice_id, float(beta),
+                      int(sweep), len(payload), zlib.crc32(payload) & 0xFFFFFFFF)
+    with open(path, "wb") as f:
+        f.write(hdr)
+        f.write(payload)
+
+
+def load_checkpoint(path: str, device="cuda"):
+    """Returns (lattice, beta, sweep); raises ValueError on a corrupted file."""
+    import struct
+    import zlib
+
+    fmt = "<8s4iiQIdQQI"
+    with open(path, "rb") as f:
+        raw = f.read()
+    n = struct.calcsize(fmt)
+    magic, d0, d1, d2, d3, prec, seed, lid, beta, sweep, nbytes, crc = struct.unpack(fmt, raw[:n])
+    payload = raw[n:]
+    if magic != _MAGIC or len(payload) != nbytes or (zlib.crc32(payload) & 0xFFFFFFFF) != crc:
+        raise ValueError(f"{path}: not an intact mgq checkpoint")
+    name = {v: k for k, v in PRECISIONS.items()}[prec]
+    lat = Lattice([d0, d1, d2, d3], name, seed=seed, lattice_id=lid, device=device)
+    if lat.links.numel() != nbytes:
+        raise ValueError(f"{path}: payload size does not match the lattice layout")
+    lat.links.copy_(torch.frombuffer(bytearray(payload), dtype=torch.uint8))
+    return lat, beta, sweep

@@ -167,6 +167,14 @@ mgq_status mgq_hmc_force(const mgq_lattice* lat, double beta, void* force_out, v
     return force_accumulate(lat, force_out, -beta / 6.0, 0.0, as_stream(stream));
 }
 
+mgq_status mgq_link_exp_update(mgq_lattice* lat, const void* alg, double s, void* stream) {
+    mgq_status st = check_lattice(lat, false, "mgq_link_exp_update");
+    if (st) return st;
+    if (!alg || ((uintptr_t)alg & 15)) return fail(MGQ_EINVAL, "mgq_link_exp_update: alg NULL or misaligned");
+    if (!(s == s)) return fail(MGQ_EINVAL, "mgq_link_exp_update: s is NaN");
+    return exp_update(lat, const_cast<void*>(alg), s, as_stream(stream));
+}
+
 mgq_status mgq_hmc_trajectory(mgq_lattice* lat, double beta, double tau, int n_steps, uint64_t traj, int accept_reject,
                               double* dH_out, int* accepted_out, void* stream) {
     mgq_status s = check_lattice(lat, true, "mgq_hmc_trajectory");

@@ -1,0 +1,52 @@
+"""torch.autograd.Function around the Wilson action whose backward is the
+hand-written force kernel: checked against central finite differences of the
+action (FP64, h = 1e-4) and against the oracle's force."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1510_04675_gb300.api import alg_to_numpy
+from paper_1510_04675_gb300.autograd import wilson_action
+
+pytestmark = pytest.mark.gpu
+
+
+def test_action_gradient_finite_differences(gpu, orc):
+    dims, beta, h = [4, 4, 4, 6], 5.7, 1e-4
+    U = orc.init_links(dims, 1, seed=12)
+    orc.update_chain(U, dims, beta, 12, 0, 0, 3, 1, 1)
+    lat = gpu.Lattice(dims, "f64")
+    lat.from_numpy(U)
+    omega = lat.new_alg_field().requires_grad_(True)
+    S = wilson_action(omega, lat, beta)
+    assert abs(S.item() - orc.action(U, dims, beta)) < 1e-9 * S.item()
+    (g,) = torch.autograd.grad(S, omega)
+    # the gradient is minus the oracle's force, link by link
+    assert np.max(np.abs(alg_to_numpy(lat, g) + orc.force(U, dims, beta))) < 1e-11
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    for _ in range(3):
+        v = torch.randn(omega.shape, dtype=torch.float64, device="cuda", generator=gen)
+        v.view(4, 2, 8, lat.site_stride)[..., lat.volume // 2:] = 0  # padding carries no links
+        fd = (wilson_action(h * v, lat, beta) - wilson_action(-h * v, lat, beta)).item() / (2 * h)
+        ad = torch.dot(g, v).item()
+        assert abs(fd - ad) < 1e-7 * max(1.0, abs(ad)), (fd, ad)
+
+
+def test_action_gradient_small_omega(gpu, orc):
+    """Away from omega = 0 the backward is the left-trivialised gradient: it
+    differs from d/domega by O(|omega|)."""
+    dims, beta, h = [4, 4, 2, 2], 6.0, 1e-5
+    lat = gpu.Lattice(dims, "f64", seed=3)
+    gpu.mgq_init_links(lat, 1)
+    gen = torch.Generator(device="cuda").manual_seed(1)
+    base = torch.randn(4 * 2 * 8 * lat.site_stride, dtype=torch.float64, device="cuda", generator=gen)
+    base.view(4, 2, 8, lat.site_stride)[..., lat.volume // 2:] = 0
+    v = torch.randn(base.shape, dtype=torch.float64, device="cuda", generator=gen)
+    v.view(4, 2, 8, lat.site_stride)[..., lat.volume // 2:] = 0
+    errs = []
+    for scale in (1e-2, 1e-3):
+        omega = (scale * base).requires_grad_(True)
+        (g,) = torch.autograd.grad(wilson_action(omega, lat, beta), omega)
+        fd = (wilson_action(omega.detach() + h * v, lat, beta) - wilson_action(omega.detach() - h * v, lat, beta)).item() / (2 * h)
+        errs.append(abs(fd - torch.dot(g, v).item()))
+    assert errs[1] < errs[0] / 5   # shrinks linearly with |omega|
