@@ -51,7 +51,7 @@ __device__ __forceinline__ Geom geom_of(const LatDesc<T>& d) {
 }
 
 template <class T, int NP, int MU>
-__global__ void __launch_bounds__(BATCH_THREADS, 4)
+__global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4)
     k_heatbath_batched(const __grid_constant__ Batch<T> B, int par, uint32_t idx_lo, uint32_t idx_hi, int n_hb) {
     const int l = find_lattice(B, blockIdx.x);
     const LatDesc<T>& d = B.d[l];
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 4)
 }
 
 template <class T, int NP, int MU>
-__global__ void __launch_bounds__(BATCH_THREADS, 4) k_overrelax_batched(const __grid_constant__ Batch<T> B, int par) {
+__global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4) k_overrelax_batched(const __grid_constant__ Batch<T> B, int par) {
     const int l = find_lattice(B, blockIdx.x);
     const LatDesc<T>& d = B.d[l];
     const int h = (blockIdx.x - B.prefix[l]) * BATCH_THREADS + threadIdx.x;

@@ -225,7 +225,7 @@ __global__ void k_export(Links<T, NP> U, Geom g, double* __restrict__ canon) {
 // that every neighbour index is resolved at compile time.  Four resident
 // blocks of 128 threads per SM (at most 128 registers) measured fastest.
 template <class T, int NP, int MU>
-__global__ void __launch_bounds__(128, 4) k_heatbath(Links<T, NP> U, Geom g, int par, T beta, RngKey rk, int n_hb,
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4) k_heatbath(Links<T, NP> U, Geom g, int par, T beta, RngKey rk, int n_hb,
                                                     uint8_t* __restrict__ dec) {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= g.Vh) return;
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(128, 4) k_heatbath(Links<T, NP> U, Geom g, int
 }
 
 template <class T, int NP, int MU>
-__global__ void __launch_bounds__(128, 4) k_overrelax(Links<T, NP> U, Geom g, int par) {
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4) k_overrelax(Links<T, NP> U, Geom g, int par) {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= g.Vh) return;
     int x[4];

@@ -302,6 +302,30 @@ __device__ __forceinline__ int lex_of(const Geom& g, const int x[4]) {
 
 __device__ __forceinline__ int wrap(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
 
+// Lexicographic offsets of the neighbours of x, wrap-around included:
+// lex(x + e_d) = lex + fwd[d], lex(x - e_d) = lex + bwd[d]; offsets of
+// different directions add (lex(x + e_mu - e_nu) = lex + fwd[mu] + bwd[nu]).
+struct Hops {
+    int lex;
+    int fwd[4], bwd[4];
+};
+
+__device__ __forceinline__ Hops make_hops(const Geom& g, const int x[4]) {
+    Hops H;
+    int st = 1;
+#pragma unroll
+    for (int d = 0; d < 4; d++) {
+        H.fwd[d] = (x[d] == g.L[d] - 1) ? -(g.L[d] - 1) * st : st;
+        H.bwd[d] = (x[d] == 0) ? (g.L[d] - 1) * st : -st;
+        st *= g.L[d];
+    }
+    H.lex = lex_of(g, x);
+    return H;
+}
+
+// a[d] for a run-time d without dynamic indexing (keeps a[] in registers)
+__device__ __forceinline__ int pick(const int a[4], int d) { return d == 0 ? a[0] : d == 1 ? a[1] : d == 2 ? a[2] : a[3]; }
+
 // Lexicographic index of x + dmu e_mu + dnu e_nu (|d| <= 1, periodic).
 // Written with compile-time array indices only, so that a run-time mu or nu
 // does not push the coordinates into local memory.

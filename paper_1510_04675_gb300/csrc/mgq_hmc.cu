@@ -14,7 +14,7 @@ namespace mgq {
 // parity = w%2), so the neighbour links of a site band are used by all
 // directions while they are still in cache.
 template <class T, int NP>
-__global__ void __launch_bounds__(256, 2) k_force(Links<T, NP> U, Geom g, Alg<T> B, T coef, T alpha) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_force(Links<T, NP> U, Geom g, Alg<T> B, T coef, T alpha) {
     const int w = threadIdx.x >> 5;
     const int mu = w >> 1, par = w & 1;
     const int h = blockIdx.x * 32 + (threadIdx.x & 31);

@@ -19,13 +19,15 @@ __device__ __forceinline__ M3<T> staple(const Links<T, NP>& U, const Geom& g, co
 #pragma unroll
         for (int j = 0; j < 3; j++) A.e[i][j] = mk(T(0), T(0));
     const int op = par ^ 1;
-    const int hpm = lex_hop(g, x, mu, +1) >> 1;
+    const Hops H = make_hops(g, x);
+    const int fmu = pick(H.fwd, mu);
+    const int hpm = (H.lex + fmu) >> 1;
 #pragma unroll
     for (int nu = 0; nu < 4; nu++) {
         if (nu == mu) continue;
-        const int hpn = lex_hop(g, x, nu, +1) >> 1;
-        const int hmn = lex_hop(g, x, nu, -1) >> 1;
-        const int hpm_mn = lex_hop(g, x, mu, +1, nu, -1) >> 1;
+        const int hpn = (H.lex + H.fwd[nu]) >> 1;
+        const int hmn = (H.lex + H.bwd[nu]) >> 1;
+        const int hpm_mn = (H.lex + fmu + H.bwd[nu]) >> 1;
         M3<T> up, dn;
         {
             const M3<T> a = U.load(nu, op, hpm);   // U_nu(x+mu)
@@ -52,20 +54,73 @@ __device__ __forceinline__ double site_plaquettes(const Links<T, NP>& U, const G
     int x[4];
     cb_coords(g, par, h, x);
     const int op = par ^ 1;
+    const Hops H = make_hops(g, x);
     double acc = 0.0;
 #pragma unroll
     for (int mu = 0; mu < 3; mu++) {
         const M3<T> umu = U.load(mu, par, h);
-        const int hpm = lex_hop(g, x, mu, +1) >> 1;
+        const int hpm = (H.lex + H.fwd[mu]) >> 1;
 #pragma unroll
         for (int nu = mu + 1; nu < 4; nu++) {
-            const int hpn = lex_hop(g, x, nu, +1) >> 1;
+            const int hpn = (H.lex + H.fwd[nu]) >> 1;
             const M3<T> a = mul_nn(umu, U.load(nu, op, hpm));
             const M3<T> b = mul_nn(U.load(nu, par, h), U.load(mu, op, hpn));
             acc += (double)retr_nd(a, b);
         }
     }
     return acc;
+}
+
+// =============================================================== SU(2) steps
+// rows i, j of m <- R(r) rows i, j, restricted to the rows (do_i, do_j) and
+// columns (bit masks ci, cj) that are read later; with the subgroup index a
+// compile-time constant the unused updates vanish.
+template <class T>
+__device__ __forceinline__ void su2_rows(M3<T>& m, int i, int j, const T r[4], bool do_i, bool do_j, int ci, int cj) {
+    const Cx<T> a = mk(r[0], r[3]), b = mk(r[2], r[1]), c = mk(-r[2], r[1]), d = mk(r[0], -r[3]);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const Cx<T> mi = m.e[i][k], mj = m.e[j][k];
+        if (do_i && ((ci >> k) & 1)) m.e[i][k] = a * mi + b * mj;
+        if (do_j && ((cj >> k) & 1)) m.e[j][k] = c * mi + d * mj;
+    }
+}
+
+// After the update of subgroup s: U needs rows 0, 1 (the final
+// reunitarisation rebuilds row 2) and, until s = 2, row 2 as an input; V only
+// needs the entries the later subgroups read (s = 1 reads row 0 and
+// V20, V22, s = 2 reads V11, V12, V21, V22).
+template <class T>
+__device__ __forceinline__ void apply_subgroup(M3<T>& u, M3<T>& v, int s, const T R[4]) {
+    if (s == 0) {
+        su2_rows(u, 0, 1, R, true, true, 7, 7);
+        su2_rows(v, 0, 1, R, true, true, 7, 6);
+    } else if (s == 1) {
+        su2_rows(u, 0, 2, R, true, true, 7, 7);
+        su2_rows(v, 0, 2, R, false, true, 0, 6);
+    } else {
+        su2_rows(u, 1, 2, R, true, false, 7, 0);
+    }
+}
+
+// Creutz's a0 and the direction (cos phi, sin phi), phi = 2 pi u3.  FP64 uses
+// the accurate library functions (the oracle's operations); FP32 uses the
+// hardware exponential, logarithm and sine/cosine where their absolute error
+// (~1e-6) is harmless, and the accurate forms near their ill-conditioned ends.
+__device__ __forceinline__ double creutz_a0(double k, double em, double u0) { return 1.0 + log1p((1.0 - u0) * em) / k; }
+__device__ __forceinline__ float creutz_a0(float k, float em, float u0) {
+    const float y = (1.f - u0) * em;
+    return 1.f + (y < -0.1f ? __logf(1.f + y) : log1pf(y)) / k;
+}
+__device__ __forceinline__ double creutz_em(double k) { return expm1(-2.0 * k); }
+__device__ __forceinline__ float creutz_em(float k) { return k > 0.25f ? __expf(-2.f * k) - 1.f : expm1f(-2.f * k); }
+__device__ __forceinline__ void creutz_phi(double u3, double* s, double* c) { sincospi(2.0 * u3, s, c); }
+__device__ __forceinline__ void creutz_phi(float u3, float* s, float* c) {
+    // 2 pi u3 - pi lies in (-pi, pi), where __sincosf is accurate; shift back by pi
+    float sn, cs;
+    __sincosf(fmaf(6.28318530718f, u3, -3.14159265359f), &sn, &cs);
+    *s = -sn;
+    *c = -cs;
 }
 
 // =============================================================== heat bath
@@ -87,25 +142,24 @@ __device__ __forceinline__ void hb_link(M3<T>& u, const M3<T>& A, T beta, int n_
         uint8_t d = 255;
         if (xi >= tiny_norm<T>()) {
             const T k = T(2) * beta * xi / T(3);
-            const T em = m_expm1(T(-2) * k);
+            const T em = creutz_em(k);
             for (int att = 0; att < n_hb; att++) {
                 const uint4 r = draw(rk, lex, mu, (uint32_t)s, (uint32_t)att, KIND_HB);
                 const T u0 = u01<T>(r.x), u1 = u01<T>(r.y), u2 = u01<T>(r.z), u3 = u01<T>(r.w);
-                const T a0 = T(1) + m_log1p((T(1) - u0) * em) / k;
+                const T a0 = creutz_a0(k, em, u0);
                 const T rest = sub_rn(T(1), mul_rn(a0, a0));
                 if (mul_rn(u1, u1) <= rest) {
                     const T rad = m_sqrt(rest);
                     const T ct = T(2) * u2 - T(1);
                     const T st = m_sqrt(sub_rn(T(1), mul_rn(ct, ct)));
                     T sp, cp;
-                    m_sincospi(T(2) * u3, &sp, &cp);
+                    creutz_phi(u3, &sp, &cp);
                     const T X[4] = {a0, rad * st * cp, rad * st * sp, rad * ct};
                     const T inv = T(1) / xi;
                     const T wh[4] = {w[0] * inv, w[1] * inv, w[2] * inv, w[3] * inv};
                     T R[4];
                     qmul(X, wh, R);
-                    left_su2(u, i, j, R);
-                    left_su2(v, i, j, R);
+                    apply_subgroup(u, v, s, R);
                     d = (uint8_t)att;
                     break;
                 }
@@ -131,8 +185,7 @@ __device__ __forceinline__ void or_link(M3<T>& u, const M3<T>& A) {
         // (w/|w|)^2 = (w0^2 - |w_vec|^2, 2 w0 w_vec) / |w|^2
         const T R[4] = {(w[0] * w[0] - w[1] * w[1] - w[2] * w[2] - w[3] * w[3]) * inv2, T(2) * w[0] * w[1] * inv2,
                         T(2) * w[0] * w[2] * inv2, T(2) * w[0] * w[3] * inv2};
-        left_su2(u, i, j, R);
-        left_su2(v, i, j, R);
+        apply_subgroup(u, v, s, R);
     }
     reunitarize(u);
 }
