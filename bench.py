@@ -53,6 +53,7 @@ def parse_args():
     p.add_argument("--therm", type=int, default=30, help="untimed thermalisation sweeps before timing")
     p.add_argument("--no-extras", action="store_true", help="skip the FP64/FP32 comparison legs")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--large", action="store_true", help="add the 48^4 FP32/FP64 leg")
     return p.parse_args()
 
 
@@ -323,6 +324,72 @@ def batched_leg(api, beta_lo=5.8, beta_hi=6.1, n_sweeps=20, n_or=4, seed=4242):
                         "1 HB + 4 OR per sweep, FP32 12-real, per-lattice FP64 plaquette"}
 
 
+def _timed(fn):
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return r, time.perf_counter() - t0
+
+
+def hmc_leg(api, dims=(24, 24, 24, 24), beta=6.0, n_traj=100, n_warm=24, n_steps=20, prec="f32c12"):
+    """HMC from a hot start: tau = 1, n_steps leapfrog steps, the first n_warm
+    trajectories without accept/reject (Sec. IV.E)."""
+    import numpy as np
+
+    lat = api.Lattice(list(dims), prec, seed=2468, with_mom=True)
+    api.mgq_init_links(lat, 1)
+    api.mgq_hmc_trajectory(lat, beta, 1.0, n_steps, 10**6, 0)  # warm the code path
+    api.mgq_init_links(lat, 1)
+    out = []
+    _, sec = _timed(lambda: [out.append(api.mgq_hmc_trajectory(lat, beta, 1.0, n_steps, t, 0 if t < n_warm else 1))
+                             for t in range(n_traj)])
+    dH = np.array([o[0] for o in out])
+    acc = np.array([o[1] for o in out])
+    return {"workload": f"{'x'.join(map(str, dims))} beta={beta} HMC, tau=1, {n_steps} steps, {n_traj} trajectories "
+                        f"from a hot start ({n_warm} without accept/reject), {prec} links, FP64 H",
+            "trajectories_per_s": n_traj / sec, "ms_per_trajectory": 1e3 * sec / n_traj,
+            "acceptance_after_warmup": float(acc[n_warm:].mean()), "final_abs_dH": float(abs(dH[-1])),
+            "plaquette": api.mgq_plaquette(lat)}
+
+
+def multiscale_leg(api, beta_c=5.7, beta_f=6.0, n_sweeps=50, prec="f32c12"):
+    """Multiscale step: coarse 8^4 (thermalised in-run) -> 16^4 prolongation with
+    the paper's 0.001 % stopping rule, 50 rethermalisation sweeps, flow to t = 1."""
+    c = api.Lattice([8, 8, 8, 8], prec, seed=1357)
+    api.mgq_init_links(c, 1)
+    api.mgq_update_sweeps(c, beta_c, 0, 100, 1, 4)
+    f = api.Lattice([16, 16, 16, 16], prec, seed=1358)
+    (iters, sd), t_pro = _timed(lambda: api.mgq_prolongate(c, f, 0.05, 1e-5, 10000))
+    p_pro = api.mgq_plaquette(f)
+    plaq, t_th = _timed(lambda: api.mgq_update_sweeps(f, beta_f, 0, n_sweeps, 1, 4, plaq_out=True))
+    (E, Q), t_fl = _timed(lambda: api.mgq_wilson_flow(f, 0.01, 100, 100))
+    return {"workload": "8^4 beta=5.7 -> 16^4 prolongation (c=0.05, 1e-5), 50 x (HB + 4 OR) at beta=6.0, "
+                        f"Wilson flow eps=0.01 to t=1, clover E and Q; {prec} links, FP64 sums",
+            "ape_iterations": iters, "ms_prolongation": 1e3 * t_pro, "ms_rethermalisation": 1e3 * t_th,
+            "ms_flow": 1e3 * t_fl, "plaquette_prolongated": p_pro, "plaquette_after": float(plaq[-1]),
+            "E_t1": float(E[-1]), "Q_t1": float(Q[-1])}
+
+
+def large_leg(api, beta=6.2):
+    """48^4 at beta = 6.2, FP32 12-real and FP64 side by side: sweeps, HMC, flow to t = 3."""
+    out = {}
+    for prec, n_sw, n_traj, n_flow in [("f32c12", 100, 10, 300), ("f64", 2, 1, 10)]:
+        lat = api.Lattice([48] * 4, prec, seed=97, with_mom=True)
+        api.mgq_init_links(lat, 1)
+        _, t_sw = _timed(lambda: api.mgq_update_sweeps(lat, beta, 0, n_sw, 1, 1))
+        _, t_h = _timed(lambda: [api.mgq_hmc_trajectory(lat, beta, 1.0, 40, t, 0) for t in range(n_traj)])
+        w = api.copy_lattice(lat)
+        _, t_f = _timed(lambda: api.mgq_wilson_flow(w, 0.01, n_flow, n_flow))
+        V = 48**4
+        out[prec] = {"sweeps": n_sw, "link_updates_per_s": 2 * 4 * V * n_sw / t_sw,
+                     "ms_per_hmc_trajectory_40_steps": 1e3 * t_h / n_traj, "ms_per_flow_step": 1e3 * t_f / n_flow}
+        del lat, w
+    return out
+
+
 def run_mgq(args, dims, world, rank, local):
     import torch
 
@@ -467,10 +534,15 @@ def run_mgq(args, dims, world, rank, local):
         out["speedup_vs_fp64"] = (value / world) / out["fp64_plain_link_updates_per_s"]
         del lat, host_links
         torch.cuda.empty_cache()
-        try:
-            out["batched"] = batched_leg(api)
-        except Exception as e:  # noqa: BLE001 - reported in the line
-            out["batched"] = {"error": str(e)[:200]}
+        legs = [("batched", batched_leg), ("hmc_24", hmc_leg), ("multiscale_16", multiscale_leg)]
+        if args.large:
+            legs.append(("large_48", large_leg))
+        for name, fn in legs:
+            try:
+                out[name] = fn(api)
+            except Exception as e:  # noqa: BLE001 - reported in the line
+                out[name] = {"error": str(e)[:200]}
+            torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample(dims, beta)
     if rank == 0:
