@@ -201,6 +201,28 @@ mgq_status mgq_topo_charge(const mgq_lattice* lat, double* E_out, double* Q_out,
 mgq_status mgq_wilson_flow(mgq_lattice* lat, double eps, int n_steps, int meas_every, double* E_out,
                            double* Q_out, void* stream);
 
+/* ---- adjoint Wilson flow (reverse mode through the RK3 step above) ------------
+ * Cotangents are algebra fields in the mom layout and precision; a cotangent
+ * L at a field W pairs with the variation W_l -> exp(e_l) W_l as
+ * sum_l sum_a L_l,a e_l,a. */
+
+/* Bytes of the caller scratch of mgq_wilson_flow_step_adjoint (2 link fields
+ * + 7 algebra fields); 0 on invalid extents or precision. */
+uint64_t mgq_flow_adjoint_scratch_bytes(const mgq_lattice* lat);
+
+/* lambda += scale * DZ(W)^T [psi]: the vector-Jacobian product of the flow
+ * generator Z(W) = -TA(W A(W)) at W = lat->links (all device, mom layout). */
+mgq_status mgq_flow_vjp(const mgq_lattice* lat, const void* psi, double scale, void* lambda, void* stream);
+
+/* One step of the adjoint flow: on entry `lambda` is a cotangent at
+ * Phi_eps(W0), the field one RK3 step of size eps after W0 = lat->links; on
+ * return it is the pulled-back cotangent at W0.  W0 is not modified; the
+ * step's intermediate fields are recomputed into `scratch` (device, 256-B
+ * aligned, >= mgq_flow_adjoint_scratch_bytes).  Errors: MGQ_EINVAL,
+ * MGQ_ENOMEM. */
+mgq_status mgq_wilson_flow_step_adjoint(const mgq_lattice* lat, double eps, void* lambda, void* scratch,
+                                        uint64_t scratch_bytes, void* stream);
+
 /* ---- HMC (Sec. IV.D, App. A) ------------------------------------------------- */
 
 /* Gauge force F(x,mu) = -(beta/6) TA(U_mu(x) A_mu(x)) into force_out

@@ -306,3 +306,21 @@ def load_checkpoint(path: str, device="cuda"):
         raise ValueError(f"{path}: payload size does not match the lattice layout")
     lat.links.copy_(torch.frombuffer(bytearray(payload), dtype=torch.uint8))
     return lat, beta, sweep
+
+
+# ------------------------------------------------------------------ adjoint flow
+def mgq_flow_vjp(lat: Lattice, psi: torch.Tensor, scale: float, lam: torch.Tensor, stream=None) -> None:
+    """lam += scale * DZ(W)^T psi for the flow generator Z(W) = -TA(W A(W)) at the lattice's links."""
+    call("mgq_flow_vjp", lat.ref, _ptr(psi), float(scale), _ptr(lam), _stream_handle(stream))
+
+
+def flow_adjoint_scratch(lat: Lattice) -> torch.Tensor:
+    n = int(_lib.load().mgq_flow_adjoint_scratch_bytes(lat.ref))
+    return torch.zeros(n, dtype=torch.uint8, device=lat.device)
+
+
+def mgq_wilson_flow_step_adjoint(lat: Lattice, eps: float, lam: torch.Tensor, scratch: torch.Tensor,
+                                 stream=None) -> None:
+    """Pull a cotangent back through one RK3 flow step that starts at the lattice's links."""
+    call("mgq_wilson_flow_step_adjoint", lat.ref, float(eps), _ptr(lam), _ptr(scratch), int(scratch.numel()),
+         _stream_handle(stream))

@@ -37,3 +37,58 @@ class WilsonAction(torch.autograd.Function):
 
 def wilson_action(omega: torch.Tensor, lat: "api.Lattice", beta: float) -> torch.Tensor:
     return WilsonAction.apply(omega, lat, beta)
+
+
+class FlowedWilsonAction(torch.autograd.Function):
+    """L(omega) = S_W(W_t), W_t the Wilson flow (n_steps fixed steps of size eps,
+    Sec. IV.B) of exp(omega) U.
+
+    Forward: the flow kernels, keeping a copy of the field every
+    `checkpoint_every` steps.  Backward: the cotangent -F(W_t) (force kernel)
+    is pulled back step by step with the adjoint-flow kernels
+    (mgq_wilson_flow_step_adjoint); each segment between checkpoints is
+    recomputed forward to recover the start of every step.  Memory: the
+    checkpoints plus one segment of link fields.
+    """
+
+    @staticmethod
+    def forward(ctx, omega, lat, beta, eps, n_steps, checkpoint_every=None):
+        import math
+
+        k = int(checkpoint_every or max(1, int(math.isqrt(max(1, n_steps)))))
+        W = api.copy_lattice(lat)
+        api.mgq_link_exp_update(W, omega.detach().contiguous(), 1.0)
+        ckpts = []
+        done = 0
+        while done < n_steps:
+            ckpts.append((done, W.links.clone()))
+            m = min(k, n_steps - done)
+            api.mgq_wilson_flow(W, eps, m, m)
+            done += m
+        plaq = api.mgq_plaquette(W)
+        ctx.W, ctx.ckpts, ctx.beta, ctx.eps, ctx.n = W, ckpts, float(beta), float(eps), int(n_steps)
+        return torch.tensor(float(beta) * 6.0 * W.volume * (1.0 - plaq), dtype=torch.float64, device=omega.device)
+
+    @staticmethod
+    def backward(ctx, grad_L):
+        W = ctx.W
+        lam = W.new_alg_field()
+        api.mgq_hmc_force(W, ctx.beta, lam)      # F = -dS/domega at W_t
+        lam.mul_(-1.0)
+        scratch = api.flow_adjoint_scratch(W)
+        seg = api.copy_lattice(W)
+        for start, links in reversed(ctx.ckpts):
+            m = min(ctx.n - start, (ctx.ckpts[1][0] - ctx.ckpts[0][0]) if len(ctx.ckpts) > 1 else ctx.n)
+            seg.links.copy_(links)
+            starts = []
+            for _ in range(m):
+                starts.append(seg.links.clone())
+                api.mgq_wilson_flow(seg, ctx.eps, 1, 2)   # one step, E/Q measured only at t = 0
+            for w0 in reversed(starts):
+                seg.links.copy_(w0)
+                api.mgq_wilson_flow_step_adjoint(seg, ctx.eps, lam, scratch)
+        return (lam.double() * grad_L).to(lam.dtype), None, None, None, None, None
+
+
+def flowed_wilson_action(omega, lat, beta, eps, n_steps, checkpoint_every=None):
+    return FlowedWilsonAction.apply(omega, lat, beta, eps, n_steps, checkpoint_every)

@@ -1,0 +1,306 @@
+// libmgq adjoint of the Wilson flow (Sec. IV.B; reverse mode through the
+// third-order Runge-Kutta step of Luscher's integrator).
+//
+// Cotangents are su(3) fields in algebra coefficients: a cotangent Lam at a
+// field W pairs with a variation W_l -> exp(eps_l) W_l as sum_l Lam_l . eps_l
+// (component dot product in the basis X_a = i lambda_a / 2, i.e. the inner
+// product <A, B> = -2 Re Tr(A B)).
+//
+// One step W0 -> W3 with Z_i = eps Z(W_i), Z(W) = -TA(W A(W)):
+//   X0 = Z0/4,                W1 = exp(X0) W0
+//   X1 = 8/9 Z1 - 17/36 Z0,   W2 = exp(X1) W1
+//   X2 = 3/4 Z2 - 8/9 Z1 + 17/36 Z0,   W3 = exp(X2) W2
+// Reverse mode, given Lam at W3:
+//   Xi2 = J(X2)* Lam;  Lam <- e^{-X2} Lam e^{X2};  Psi2 = 3/4 Xi2;                     Lam += eps DZ(W2)*[Psi2]
+//   Xi1 = J(X1)* Lam;  Lam <- e^{-X1} Lam e^{X1};  Psi1 = 8/9 (Xi1 - Xi2);             Lam += eps DZ(W1)*[Psi1]
+//   Xi0 = J(X0)* Lam;  Lam <- e^{-X0} Lam e^{X0};  Psi0 = Xi0/4 - 17/36 (Xi1 - Xi2);   Lam += eps DZ(W0)*[Psi0]
+// with J(X)* = sum_n (-ad_X)^n / (n+1)!, the adjoint of the differential of
+// exp (d/dt e^{X + tY} e^{-X} = sum_n ad_X^n Y / (n+1)!).
+#include "mgq_internal.h"
+#include "mgq_stencil.cuh"
+
+namespace mgq {
+
+mgq_status force_accumulate(const mgq_lattice* lat, void* B, double coef, double alpha, cudaStream_t st);
+mgq_status exp_update(const mgq_lattice* lat, void* B, double s, cudaStream_t st);
+
+// i Q for hermitian Q: the antihermitian matrix sum_a c_a X_a
+template <class T> __device__ __forceinline__ M3<T> alg_matrix(const T c[8]) {
+    const M3<T> q = herm_from_coeffs(c);
+    M3<T> r;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) r.e[i][j] = mk(-q.e[i][j].im, q.e[i][j].re);
+    return r;
+}
+
+template <class T> __device__ __forceinline__ M3<T> commutator(const M3<T>& a, const M3<T>& b) {
+    M3<T> ab = mul_nn(a, b), ba = mul_nn(b, a);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) ab.e[i][j] = ab.e[i][j] - ba.e[i][j];
+    return ab;
+}
+
+// Per link: X = c0 Z0 + c1 Z1 + c2 Z2; Xi = J(X)* Lam (series, 12 terms:
+// |X| is O(eps)); Lam <- e^{-X} Lam e^{X}.
+template <class T>
+__global__ void __launch_bounds__(128) k_dexp_adjoint(Geom g, Alg<T> Z0, Alg<T> Z1, Alg<T> Z2, T c0, T c1, T c2,
+                                                      Alg<T> Lam, Alg<T> Xi) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 8 * g.Vh) return;
+    const int mp = idx / g.Vh, h = idx - mp * g.Vh, mu = mp >> 1, par = mp & 1;
+    T z0[8], z1[8], z2[8], x[8], l[8];
+    Z0.load(mu, par, h, z0);
+    Z1.load(mu, par, h, z1);
+    Z2.load(mu, par, h, z2);
+    Lam.load(mu, par, h, l);
+#pragma unroll
+    for (int a = 0; a < 8; a++) x[a] = c0 * z0[a] + c1 * z1[a] + c2 * z2[a];
+    const M3<T> X = alg_matrix(x);
+    const M3<T> L = alg_matrix(l);
+    M3<T> term = L, sum = L;
+#pragma unroll 1
+    for (int n = 1; n <= 12; n++) {
+        term = commutator(X, term);
+        const T f = T(-1) / T(n + 1);
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                term.e[i][j] = scale(term.e[i][j], f);
+                sum.e[i][j] = sum.e[i][j] + term.e[i][j];
+            }
+    }
+    T xi[8];
+    ta_coeffs(sum, xi);
+    Xi.store(mu, par, h, xi);
+    const M3<T> E = exp_alg(x);
+    const M3<T> Ln = mul_dn(E, mul_nn(L, E));
+    T ln[8];
+    ta_coeffs(Ln, ln);
+    Lam.store(mu, par, h, ln);
+}
+
+// P <- a0 X0 + a1 X1 + a2 X2 (algebra coefficients, elementwise)
+template <class T>
+__global__ void k_alg_combine(Geom g, Alg<T> P, Alg<T> X0, Alg<T> X1, Alg<T> X2, T a0, T a1, T a2) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 8 * g.Vh) return;
+    const int mp = idx / g.Vh, h = idx - mp * g.Vh, mu = mp >> 1, par = mp & 1;
+    T p[8], u[8], v[8], w[8];
+    X0.load(mu, par, h, u);
+    X1.load(mu, par, h, v);
+    X2.load(mu, par, h, w);
+#pragma unroll
+    for (int a = 0; a < 8; a++) p[a] = a0 * u[a] + a1 * v[a] + a2 * w[a];
+    P.store(mu, par, h, p);
+}
+
+template <class T, int NP>
+__device__ __forceinline__ M3<T> psi_at(const Alg<T>& P, int mu, int par, int h) {
+    T c[8];
+    P.load(mu, par, h, c);
+    return alg_matrix(c);
+}
+
+// Lam_m += scale * DZ(W)*[Psi]_m for every link m = U_rho(y): the self term
+// -TA(W_m A_m Psi_m) and, for each staple factor equal to U_m in the
+// staples of the 18 links that contain it, -TA(U_m (rest of the loop with
+// Psi W inserted)) for an undaggered factor, +TA((rest) U_m^+) for a
+// daggered one.
+template <class T, int NP>
+__global__ void __launch_bounds__(128) k_flow_vjp(Links<T, NP> U, Geom g, Alg<T> Psi, T scl, Alg<T> Lam) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 8 * g.Vh) return;
+    const int mp = idx / g.Vh, h = idx - mp * g.Vh, rho = mp >> 1, par = mp & 1;
+    const int op = par ^ 1;
+    int x[4];
+    cb_coords(g, par, h, x);
+    const Hops H = make_hops(g, x);
+    const M3<T> Um = U.load(rho, par, h);
+    T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    auto add = [&](const M3<T>& N, T sgn) {
+        T t[8];
+        ta_coeffs(N, t);
+#pragma unroll
+        for (int a = 0; a < 8; a++) acc[a] += sgn * t[a];
+    };
+    // (1) self
+    {
+        const M3<T> A = staple(U, g, x, h, rho, par);
+        add(mul_nn(mul_nn(Um, A), psi_at<T, NP>(Psi, rho, par, h)), T(-1));
+    }
+    const int frho = pick(H.fwd, rho), brho = pick(H.bwd, rho);
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        if (mu == rho) continue;
+        const int fmu = H.fwd[mu], bmu = H.bwd[mu];
+        const int l_mm = H.lex + bmu;                // y - mu       (parity op)
+        const int l_mm_pr = H.lex + bmu + frho;      // y - mu + rho (parity par)
+        const int l_pr = H.lex + frho;               // y + rho      (op)
+        const int l_pm = H.lex + fmu;                // y + mu       (op)
+        // (2) l = U_mu(y-mu): -TA(U_rho(y) U_mu(y-mu+rho)^+ U_rho(y-mu)^+ Psi_mu(y-mu) U_mu(y-mu))
+        {
+            const M3<T> a = mul_nd(mul_nd(Um, U.load(mu, par, l_mm_pr >> 1)), U.load(rho, op, l_mm >> 1));
+            add(mul_nn(mul_nn(a, psi_at<T, NP>(Psi, mu, op, l_mm >> 1)), U.load(mu, op, l_mm >> 1)), T(-1));
+        }
+        // (3) l = U_mu(y): +TA(Psi_mu(y) U_mu(y) U_rho(y+mu) U_mu(y+rho)^+ U_rho(y)^+)
+        {
+            const M3<T> a = mul_nn(mul_nn(psi_at<T, NP>(Psi, mu, par, h), U.load(mu, par, h)), U.load(rho, op, l_pm >> 1));
+            add(mul_nd(mul_nd(a, U.load(mu, op, l_pr >> 1)), Um), T(1));
+        }
+        // (4) l = U_mu(y-mu+rho): +TA(U_mu(y-mu)^+ U_rho(y-mu) Psi_mu(y-mu+rho) U_mu(y-mu+rho) U_rho(y)^+)
+        {
+            const M3<T> a = mul_dn(U.load(mu, op, l_mm >> 1), U.load(rho, op, l_mm >> 1));
+            const M3<T> b = mul_nn(mul_nn(a, psi_at<T, NP>(Psi, mu, par, l_mm_pr >> 1)), U.load(mu, par, l_mm_pr >> 1));
+            add(mul_nd(b, Um), T(1));
+        }
+        // (5) l = U_mu(y+rho): -TA(U_rho(y) Psi_mu(y+rho) U_mu(y+rho) U_rho(y+mu)^+ U_mu(y)^+)
+        {
+            const M3<T> a = mul_nn(mul_nn(Um, psi_at<T, NP>(Psi, mu, op, l_pr >> 1)), U.load(mu, op, l_pr >> 1));
+            add(mul_nd(mul_nd(a, U.load(rho, op, l_pm >> 1)), U.load(mu, par, h)), T(-1));
+        }
+    }
+#pragma unroll
+    for (int nu = 0; nu < 4; nu++) {
+        if (nu == rho) continue;
+        const int fnu = H.fwd[nu], bnu = H.bwd[nu];
+        const int l_mn = H.lex + bnu;               // y - nu        (op)
+        const int l_mn_pr = H.lex + bnu + frho;     // y - nu + rho  (par)
+        const int l_pn = H.lex + fnu;               // y + nu        (op)
+        const int l_pr_ = H.lex + frho;             // y + rho       (op)
+        // (6) l = U_rho(y-nu): +TA(U_nu(y-nu)^+ Psi_rho(y-nu) U_rho(y-nu) U_nu(y-nu+rho) U_rho(y)^+)
+        {
+            const M3<T> a = mul_dn(U.load(nu, op, l_mn >> 1), psi_at<T, NP>(Psi, rho, op, l_mn >> 1));
+            const M3<T> b = mul_nn(mul_nn(a, U.load(rho, op, l_mn >> 1)), U.load(nu, par, l_mn_pr >> 1));
+            add(mul_nd(b, Um), T(1));
+        }
+        // (7) l = U_rho(y+nu): +TA(U_nu(y) Psi_rho(y+nu) U_rho(y+nu) U_nu(y+rho)^+ U_rho(y)^+)
+        {
+            const M3<T> a = mul_nn(mul_nn(U.load(nu, par, h), psi_at<T, NP>(Psi, rho, op, l_pn >> 1)), U.load(rho, op, l_pn >> 1));
+            add(mul_nd(mul_nd(a, U.load(nu, op, l_pr_ >> 1)), Um), T(1));
+        }
+    }
+    (void)brho;
+    T* b = Lam.at(rho, par, h);
+#pragma unroll
+    for (int a = 0; a < 8; a++) b[(size_t)a * Lam.S] += scl * acc[a];
+}
+
+static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
+
+static mgq_status flow_vjp(const mgq_lattice* lat, const void* links, const void* psi, double scl, void* lam,
+                           cudaStream_t st) {
+    const Geom g = make_geom(lat->dims);
+    dispatch_prec(lat->prec, [&]<class T, int NP>() {
+        k_flow_vjp<T, NP><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(
+            links_at<T, NP>(const_cast<void*>(links), lat->dims), g, alg_at<T>(const_cast<void*>(psi), lat->dims),
+            (T)scl, alg_at<T>(lam, lat->dims));
+    });
+    return cuda_check("flow_vjp");
+}
+
+static mgq_status dexp_adjoint(const mgq_lattice* lat, void* z0, void* z1, void* z2, double c0, double c1, double c2,
+                               void* lam, void* xi, cudaStream_t st) {
+    const Geom g = make_geom(lat->dims);
+    if (lat->prec == MGQ_F64)
+        k_dexp_adjoint<double><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(
+            g, alg_at<double>(z0, lat->dims), alg_at<double>(z1, lat->dims), alg_at<double>(z2, lat->dims), c0, c1, c2,
+            alg_at<double>(lam, lat->dims), alg_at<double>(xi, lat->dims));
+    else
+        k_dexp_adjoint<float><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(
+            g, alg_at<float>(z0, lat->dims), alg_at<float>(z1, lat->dims), alg_at<float>(z2, lat->dims), (float)c0,
+            (float)c1, (float)c2, alg_at<float>(lam, lat->dims), alg_at<float>(xi, lat->dims));
+    return cuda_check("dexp_adjoint");
+}
+
+static mgq_status combine(const mgq_lattice* lat, void* p, void* x0, void* x1, void* x2, double a0, double a1,
+                          double a2, cudaStream_t st) {
+    const Geom g = make_geom(lat->dims);
+    if (lat->prec == MGQ_F64)
+        k_alg_combine<double><<<nblk(8L * g.Vh, 256), 256, 0, st>>>(
+            g, alg_at<double>(p, lat->dims), alg_at<double>(x0, lat->dims), alg_at<double>(x1, lat->dims),
+            alg_at<double>(x2, lat->dims), a0, a1, a2);
+    else
+        k_alg_combine<float><<<nblk(8L * g.Vh, 256), 256, 0, st>>>(
+            g, alg_at<float>(p, lat->dims), alg_at<float>(x0, lat->dims), alg_at<float>(x1, lat->dims),
+            alg_at<float>(x2, lat->dims), (float)a0, (float)a1, (float)a2);
+    return cuda_check("combine");
+}
+
+uint64_t flow_adjoint_scratch(const mgq_lattice* lat) {
+    return 2 * round256(links_bytes(lat)) + 7 * round256(alg_bytes(lat));
+}
+
+}  // namespace mgq
+
+using namespace mgq;
+
+extern "C" {
+
+uint64_t mgq_flow_adjoint_scratch_bytes(const mgq_lattice* lat) {
+    if (!lat || !links_bytes(lat)) return 0;
+    return flow_adjoint_scratch(lat);
+}
+
+mgq_status mgq_flow_vjp(const mgq_lattice* lat, const void* psi, double scale, void* lambda, void* stream) {
+    mgq_status s = check_lattice(lat, false, "mgq_flow_vjp");
+    if (s) return s;
+    if (!psi || !lambda || ((uintptr_t)psi & 15) || ((uintptr_t)lambda & 15))
+        return fail(MGQ_EINVAL, "mgq_flow_vjp: psi/lambda NULL or misaligned");
+    return flow_vjp(lat, lat->links, psi, scale, lambda, as_stream(stream));
+}
+
+mgq_status mgq_wilson_flow_step_adjoint(const mgq_lattice* lat, double eps, void* lambda, void* scratch,
+                                        uint64_t scratch_bytes, void* stream) {
+    mgq_status s = check_lattice(lat, false, "mgq_wilson_flow_step_adjoint");
+    if (s) return s;
+    if (!(eps > 0.0)) return fail(MGQ_EINVAL, "mgq_wilson_flow_step_adjoint: eps must be > 0");
+    if (!lambda || ((uintptr_t)lambda & 15)) return fail(MGQ_EINVAL, "mgq_wilson_flow_step_adjoint: lambda NULL or misaligned");
+    if (!scratch || ((uintptr_t)scratch & 255)) return fail(MGQ_EINVAL, "mgq_wilson_flow_step_adjoint: scratch NULL or not 256-byte aligned");
+    if (scratch_bytes < flow_adjoint_scratch(lat))
+        return fail(MGQ_ENOMEM, "mgq_wilson_flow_step_adjoint: scratch has %llu bytes, needs %llu",
+                    (unsigned long long)scratch_bytes, (unsigned long long)flow_adjoint_scratch(lat));
+    cudaStream_t st = as_stream(stream);
+    const uint64_t lb = round256(links_bytes(lat)), ab = round256(alg_bytes(lat));
+    char* p = static_cast<char*>(scratch);
+    void* W1 = p;
+    void* W2 = p + lb;
+    void* Z[3] = {p + 2 * lb, p + 2 * lb + ab, p + 2 * lb + 2 * ab};
+    void* Xi[3] = {p + 2 * lb + 3 * ab, p + 2 * lb + 4 * ab, p + 2 * lb + 5 * ab};
+    void* Psi = p + 2 * lb + 6 * ab;
+    const uint64_t lbytes = links_bytes(lat), abytes = alg_bytes(lat);
+    // forward recompute of the step from W0 = lat->links (left unchanged)
+    mgq_lattice w = *lat;
+    if ((s = force_accumulate(lat, Z[0], -eps, 0.0, st))) return s;  // Z0 = eps Z(W0)
+    if (cudaMemcpyAsync(W1, lat->links, lbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return cuda_check("mgq_wilson_flow_step_adjoint");
+    w.links = W1;
+    if ((s = exp_update(&w, Z[0], 0.25, st))) return s;                   // W1 = exp(Z0/4) W0
+    if ((s = force_accumulate(&w, Z[1], -eps, 0.0, st))) return s;        // Z1 = eps Z(W1)
+    if (cudaMemcpyAsync(W2, W1, lbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return cuda_check("mgq_wilson_flow_step_adjoint");
+    w.links = W2;
+    if ((s = combine(lat, Psi, Z[0], Z[1], Z[1], -17.0 / 36.0, 8.0 / 9.0, 0.0, st))) return s;  // X1
+    if ((s = exp_update(&w, Psi, 1.0, st))) return s;                     // W2 = exp(X1) W1
+    if ((s = force_accumulate(&w, Z[2], -eps, 0.0, st))) return s;        // Z2 = eps Z(W2)
+    // reverse stage 2
+    if ((s = dexp_adjoint(lat, Z[0], Z[1], Z[2], 17.0 / 36.0, -8.0 / 9.0, 0.75, lambda, Xi[2], st))) return s;
+    if ((s = combine(lat, Psi, Xi[2], Xi[2], Xi[2], 0.75, 0.0, 0.0, st))) return s;
+    if ((s = flow_vjp(lat, W2, Psi, eps, lambda, st))) return s;
+    // reverse stage 1
+    if ((s = dexp_adjoint(lat, Z[0], Z[1], Z[2], -17.0 / 36.0, 8.0 / 9.0, 0.0, lambda, Xi[1], st))) return s;
+    if ((s = combine(lat, Psi, Xi[1], Xi[2], Xi[2], 8.0 / 9.0, -8.0 / 9.0, 0.0, st))) return s;
+    if ((s = flow_vjp(lat, W1, Psi, eps, lambda, st))) return s;
+    // reverse stage 0
+    if ((s = dexp_adjoint(lat, Z[0], Z[1], Z[2], 0.25, 0.0, 0.0, lambda, Xi[0], st))) return s;
+    if ((s = combine(lat, Psi, Xi[0], Xi[1], Xi[2], 0.25, -17.0 / 36.0, 17.0 / 36.0, st))) return s;
+    if ((s = flow_vjp(lat, lat->links, Psi, eps, lambda, st))) return s;
+    (void)abytes;
+    return MGQ_OK;
+}
+
+}  // extern "C"

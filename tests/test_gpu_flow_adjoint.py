@@ -1,0 +1,92 @@
+"""Adjoint Wilson flow: the vector-Jacobian product of the flow generator, one
+reverse RK3 step, and the checkpointed multi-step autograd.Function, all
+against central finite differences of forward quantities (FP64)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1510_04675_gb300.autograd import flowed_wilson_action
+
+pytestmark = pytest.mark.gpu
+
+
+def _field(gpu, dims, seed, sweeps=2):
+    lat = gpu.Lattice(dims, "f64", seed=seed)
+    gpu.mgq_init_links(lat, 1)
+    gpu.mgq_update_sweeps(lat, 6.0, 0, sweeps, 1, 1)
+    return lat
+
+
+def _rand_alg(lat, gen, scale=1.0):
+    v = torch.randn(4 * 2 * 8 * lat.site_stride, dtype=torch.float64, device="cuda", generator=gen) * scale
+    v.view(4, 2, 8, lat.site_stride)[..., lat.volume // 2:] = 0
+    return v
+
+
+def _Z(gpu, lat):
+    F = lat.new_alg_field()
+    gpu.mgq_hmc_force(lat, 6.0, F)   # -(6/6) TA(W A) = Z(W)
+    return F
+
+
+def _moved(gpu, lat, v, h):
+    m = gpu.copy_lattice(lat)
+    gpu.mgq_link_exp_update(m, v, h)
+    return m
+
+
+def test_generator_vjp_matches_finite_differences(gpu):
+    lat = _field(gpu, [4, 4, 2, 4], 3)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    psi, v = _rand_alg(lat, gen), _rand_alg(lat, gen)
+    lam = lat.new_alg_field()
+    gpu.mgq_flow_vjp(lat, psi, 1.0, lam)
+    h = 1e-5
+    dZ = (_Z(gpu, _moved(gpu, lat, v, h)) - _Z(gpu, _moved(gpu, lat, v, -h))) / (2 * h)
+    fd = torch.dot(psi, dZ).item()
+    ad = torch.dot(lam, v).item()
+    assert abs(fd - ad) < 1e-7 * max(1.0, abs(fd)), (fd, ad)
+
+
+def _action(gpu, lat, beta=6.0):
+    return beta * 6 * lat.volume * (1 - gpu.mgq_plaquette(lat))
+
+
+def test_one_step_adjoint(gpu):
+    lat = _field(gpu, [4, 4, 4, 2], 7)
+    eps = 0.05
+    W = gpu.copy_lattice(lat)
+    gpu.mgq_wilson_flow(W, eps, 1, 2)
+    lam = W.new_alg_field()
+    gpu.mgq_hmc_force(W, 6.0, lam)
+    lam.mul_(-1.0)                                   # dS/domega at W_eps
+    scratch = gpu.flow_adjoint_scratch(lat)
+    gpu.mgq_wilson_flow_step_adjoint(lat, eps, lam, scratch)
+    gen = torch.Generator(device="cuda").manual_seed(9)
+    v = _rand_alg(lat, gen)
+    h = 1e-5
+
+    def L(sign):
+        m = _moved(gpu, lat, v, sign * h)
+        gpu.mgq_wilson_flow(m, eps, 1, 2)
+        return _action(gpu, m)
+
+    fd = (L(1) - L(-1)) / (2 * h)
+    ad = torch.dot(lam, v).item()
+    assert abs(fd - ad) < 1e-6 * max(1.0, abs(fd)), (fd, ad)
+
+
+@pytest.mark.parametrize("n_steps,every", [(10, 3), (6, 6)])
+def test_checkpointed_flow_gradient(gpu, n_steps, every):
+    lat = _field(gpu, [4, 4, 4, 4], 11)
+    eps, beta = 0.02, 6.0
+    omega = lat.new_alg_field().requires_grad_(True)
+    L0 = flowed_wilson_action(omega, lat, beta, eps, n_steps, every)
+    (g,) = torch.autograd.grad(L0, omega)
+    gen = torch.Generator(device="cuda").manual_seed(13)
+    v = _rand_alg(lat, gen)
+    h = 1e-5
+    fd = (flowed_wilson_action(h * v, lat, beta, eps, n_steps).item()
+          - flowed_wilson_action(-h * v, lat, beta, eps, n_steps).item()) / (2 * h)
+    ad = torch.dot(g, v).item()
+    assert abs(fd - ad) < 1e-6 * max(1.0, abs(fd)), (fd, ad)
