@@ -116,107 +116,52 @@ template <class T> __device__ __forceinline__ M3<T> mul_dd(const M3<T>& a, const
 }
 // FP32 products on the packed f32x2 FMA of sm_100+: a complex product is
 // a.re * (b.re, b.im) + a.im * (-b.im, b.re), two paired FMAs instead of four.
+// ROWS = 2 computes rows 0 and 1 of the result only; DA / DB take the
+// conjugate transpose of a / b.
 __device__ __forceinline__ float2 bcast(float x) { return make_float2(x, x); }
 __device__ __forceinline__ Cx<float> from_f2(float2 z) { return mk(z.x, z.y); }
 
+template <int ROWS, bool DA, bool DB>
+__device__ __forceinline__ M3<float> x2_product(const M3<float>& a, const M3<float>& b) {
+    float2 B[3][3], iB[3][3];  // B[k][j] = (b_kj or conj(b_jk)), iB = i B
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float re = DB ? b.e[j][k].re : b.e[k][j].re;
+            const float im = DB ? -b.e[j][k].im : b.e[k][j].im;
+            B[k][j] = make_float2(re, im);
+            iB[k][j] = make_float2(-im, re);
+        }
+    M3<float> r;
+#pragma unroll
+    for (int i = 0; i < ROWS; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float are = DA ? a.e[k][i].re : a.e[i][k].re;
+                const float aim = DA ? -a.e[k][i].im : a.e[i][k].im;
+                acc = __ffma2_rn(bcast(are), B[k][j], acc);
+                acc = __ffma2_rn(bcast(aim), iB[k][j], acc);
+            }
+            r.e[i][j] = from_f2(acc);
+        }
+    return r;
+}
+
 template <> __device__ __forceinline__ M3<float> mul_nn<float>(const M3<float>& a, const M3<float>& b) {
-    float2 B[3][3], iB[3][3];
-#pragma unroll
-    for (int k = 0; k < 3; k++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            B[k][j] = make_float2(b.e[k][j].re, b.e[k][j].im);
-            iB[k][j] = make_float2(-b.e[k][j].im, b.e[k][j].re);
-        }
-    M3<float> r;
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                acc = __ffma2_rn(bcast(a.e[i][k].re), B[k][j], acc);
-                acc = __ffma2_rn(bcast(a.e[i][k].im), iB[k][j], acc);
-            }
-            r.e[i][j] = from_f2(acc);
-        }
-    return r;
+    return x2_product<3, false, false>(a, b);
 }
-// a b^+ : sum_k a_ik conj(b_jk) = a.re * conj(b) + a.im * (b.im, b.re)
 template <> __device__ __forceinline__ M3<float> mul_nd<float>(const M3<float>& a, const M3<float>& b) {
-    float2 C[3][3], iC[3][3];
-#pragma unroll
-    for (int j = 0; j < 3; j++)
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            C[j][k] = make_float2(b.e[j][k].re, -b.e[j][k].im);
-            iC[j][k] = make_float2(b.e[j][k].im, b.e[j][k].re);
-        }
-    M3<float> r;
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                acc = __ffma2_rn(bcast(a.e[i][k].re), C[j][k], acc);
-                acc = __ffma2_rn(bcast(a.e[i][k].im), iC[j][k], acc);
-            }
-            r.e[i][j] = from_f2(acc);
-        }
-    return r;
+    return x2_product<3, false, true>(a, b);
 }
-// a^+ b : sum_k conj(a_ki) b_kj = a.re * b - a.im * (-b.im, b.re)
 template <> __device__ __forceinline__ M3<float> mul_dn<float>(const M3<float>& a, const M3<float>& b) {
-    float2 B[3][3], iB[3][3];
-#pragma unroll
-    for (int k = 0; k < 3; k++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            B[k][j] = make_float2(b.e[k][j].re, b.e[k][j].im);
-            iB[k][j] = make_float2(-b.e[k][j].im, b.e[k][j].re);
-        }
-    M3<float> r;
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                acc = __ffma2_rn(bcast(a.e[k][i].re), B[k][j], acc);
-                acc = __ffma2_rn(bcast(-a.e[k][i].im), iB[k][j], acc);
-            }
-            r.e[i][j] = from_f2(acc);
-        }
-    return r;
+    return x2_product<3, true, false>(a, b);
 }
-// a^+ b^+ : sum_k conj(a_ki) conj(b_jk) = a.re * conj(b) - a.im * (b.im, b.re)
 template <> __device__ __forceinline__ M3<float> mul_dd<float>(const M3<float>& a, const M3<float>& b) {
-    float2 C[3][3], iC[3][3];
-#pragma unroll
-    for (int j = 0; j < 3; j++)
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            C[j][k] = make_float2(b.e[j][k].re, -b.e[j][k].im);
-            iC[j][k] = make_float2(b.e[j][k].im, b.e[j][k].re);
-        }
-    M3<float> r;
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                acc = __ffma2_rn(bcast(a.e[k][i].re), C[j][k], acc);
-                acc = __ffma2_rn(bcast(-a.e[k][i].im), iC[j][k], acc);
-            }
-            r.e[i][j] = from_f2(acc);
-        }
-    return r;
+    return x2_product<3, true, true>(a, b);
 }
 
 template <class T> __device__ __forceinline__ void acc_add(M3<T>& a, const M3<T>& b) {
@@ -365,6 +310,16 @@ struct Links {
 #pragma unroll
             for (int c = 0; c < 3; c++) m.e[r][c] = ldg_cx(b + (size_t)(r * 3 + c) * S);
         if (NP == 6) rebuild_row2(m);
+        return m;
+    }
+    // rows 0 and 1 only (row 2 left unset), for factors whose third row is not read
+    __device__ __forceinline__ M3<T> load_rows(int mu, int par, int h) const {
+        const Cx<T>* b = base(mu, par, h);
+        M3<T> m;
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) m.e[r][c] = ldg_cx(b + (size_t)(r * 3 + c) * S);
         return m;
     }
     // load of a link given its lexicographic site (parity from the site)

@@ -6,13 +6,100 @@
 
 namespace mgq {
 
+// Rows 0 and 1 of a b^+ and of a b (row 2 of the result is left unset): the
+// callers rebuild it as conj(row0 x row1) because the product is in SU(3).
+template <class T> __device__ __forceinline__ M3<T> mul_nd_2(const M3<T>& a, const M3<T>& b) {
+    M3<T> r;
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            r.e[i][j] = mulc(a.e[i][0], b.e[j][0]) + mulc(a.e[i][1], b.e[j][1]) + mulc(a.e[i][2], b.e[j][2]);
+    return r;
+}
+template <class T> __device__ __forceinline__ M3<T> mul_nn_2(const M3<T>& a, const M3<T>& b) {
+    M3<T> r;
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) r.e[i][j] = a.e[i][0] * b.e[0][j] + a.e[i][1] * b.e[1][j] + a.e[i][2] * b.e[2][j];
+    return r;
+}
+// rows 0, 1 of a^+ b
+template <class T> __device__ __forceinline__ M3<T> mul_dn_2(const M3<T>& a, const M3<T>& b) {
+    M3<T> r;
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            r.e[i][j] = mulc(b.e[0][j], a.e[0][i]) + mulc(b.e[1][j], a.e[1][i]) + mulc(b.e[2][j], a.e[2][i]);
+    return r;
+}
+
+template <> __device__ __forceinline__ M3<float> mul_nd_2<float>(const M3<float>& a, const M3<float>& b) {
+    return x2_product<2, false, true>(a, b);
+}
+template <> __device__ __forceinline__ M3<float> mul_nn_2<float>(const M3<float>& a, const M3<float>& b) {
+    return x2_product<2, false, false>(a, b);
+}
+template <> __device__ __forceinline__ M3<float> mul_dn_2<float>(const M3<float>& a, const M3<float>& b) {
+    return x2_product<2, true, false>(a, b);
+}
+
 // =============================================================== staple
 // A_mu(x) = sum_{nu != mu} [ U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
 //                          + U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu) ]
 // so that Re Tr(U_mu(x) A_mu(x)) sums the six plaquettes holding U_mu(x).
 // x has parity par; x +- e_nu has parity 1 - par, x + e_mu - e_nu parity par.
+//
+// Staple for two-row (12-real) links.  Each staple term is a product of three
+// SU(3) links, hence in SU(3): only rows 0, 1 of every partial product are
+// computed and row 2 is rebuilt, and a link that enters only through its rows
+// (the left factor) is never completed.
+//   up = (a b^+) c^+            a = U_nu(x+mu), b = U_mu(x+nu), c = U_nu(x)
+//   dn = (e d)^+ f              d = U_nu(x+mu-nu), e = U_mu(x-nu), f = U_nu(x-nu)
+template <class T>
+__device__ __forceinline__ M3<T> staple_two_row(const Links<T, 6>& U, const Geom& g, const int x[4], int h, int mu,
+                                                int par) {
+    M3<T> A;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) A.e[i][j] = mk(T(0), T(0));
+    const int op = par ^ 1;
+    const Hops H = make_hops(g, x);
+    const int fmu = pick(H.fwd, mu);
+    const int hpm = (H.lex + fmu) >> 1;
+#pragma unroll
+    for (int nu = 0; nu < 4; nu++) {
+        if (nu == mu) continue;
+        const int hpn = (H.lex + H.fwd[nu]) >> 1;
+        const int hmn = (H.lex + H.bwd[nu]) >> 1;
+        const int hpm_mn = (H.lex + fmu + H.bwd[nu]) >> 1;
+        M3<T> up, dn;
+        {
+            M3<T> t = mul_nd_2(U.load_rows(nu, op, hpm), U.load(mu, op, hpn));
+            rebuild_row2(t);
+            up = mul_nd_2(t, U.load(nu, par, h));
+            rebuild_row2(up);
+        }
+        {
+            M3<T> t = mul_nn_2(U.load_rows(mu, op, hmn), U.load(nu, par, hpm_mn));
+            rebuild_row2(t);
+            dn = mul_dn_2(t, U.load(nu, op, hmn));
+            rebuild_row2(dn);
+        }
+        acc_add(up, dn);
+        acc_add(A, up);
+    }
+    return A;
+}
+
 template <class T, int NP>
 __device__ __forceinline__ M3<T> staple(const Links<T, NP>& U, const Geom& g, const int x[4], int h, int mu, int par) {
+    if constexpr (NP == 6) {
+        return staple_two_row(U, g, x, h, mu, par);
+    }
     M3<T> A;
 #pragma unroll
     for (int i = 0; i < 3; i++)
