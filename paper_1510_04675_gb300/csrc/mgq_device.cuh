@@ -170,6 +170,13 @@ template <class T> __device__ __forceinline__ void acc_add(M3<T>& a, const M3<T>
 #pragma unroll
         for (int j = 0; j < 3; j++) a.e[i][j] = a.e[i][j] + b.e[i][j];
 }
+template <> __device__ __forceinline__ void acc_add<float>(M3<float>& a, const M3<float>& b) {
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            a.e[i][j] = from_f2(__fadd2_rn(make_float2(a.e[i][j].re, a.e[i][j].im), make_float2(b.e[i][j].re, b.e[i][j].im)));
+}
 template <class T> __device__ __forceinline__ M3<T> dagger(const M3<T>& a) {
     M3<T> r;
 #pragma unroll
@@ -202,6 +209,26 @@ template <class T> __device__ __forceinline__ void rebuild_row2(M3<T>& u) {
     u.e[2][0] = conjg(u.e[0][1] * u.e[1][2] - u.e[0][2] * u.e[1][1]);
     u.e[2][1] = conjg(u.e[0][2] * u.e[1][0] - u.e[0][0] * u.e[1][2]);
     u.e[2][2] = conjg(u.e[0][0] * u.e[1][1] - u.e[0][1] * u.e[1][0]);
+}
+
+// FP32: conj(a b - c d) per entry on the packed FMA, row 1 entries paired.
+template <> __device__ __forceinline__ void rebuild_row2<float>(M3<float>& u) {
+    float2 B[3], iB[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        B[k] = make_float2(u.e[1][k].re, u.e[1][k].im);
+        iB[k] = make_float2(-u.e[1][k].im, u.e[1][k].re);
+    }
+    // entry k: row0[p] row1[q] - row0[q] row1[p] with (p, q) = (1,2), (2,0), (0,1)
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const int p = (k + 1) % 3, q = (k + 2) % 3;
+        float2 acc = __fmul2_rn(bcast(u.e[0][p].re), B[q]);
+        acc = __ffma2_rn(bcast(u.e[0][p].im), iB[q], acc);
+        acc = __ffma2_rn(bcast(-u.e[0][q].re), B[p], acc);
+        acc = __ffma2_rn(bcast(-u.e[0][q].im), iB[p], acc);
+        u.e[2][k] = mk(acc.x, -acc.y);
+    }
 }
 
 // Gram-Schmidt reunitarisation: normalise row 0, orthogonalise and

@@ -52,14 +52,14 @@ template <> __device__ __forceinline__ M3<float> mul_dn_2<float>(const M3<float>
 // so that Re Tr(U_mu(x) A_mu(x)) sums the six plaquettes holding U_mu(x).
 // x has parity par; x +- e_nu has parity 1 - par, x + e_mu - e_nu parity par.
 //
-// Staple for two-row (12-real) links.  Each staple term is a product of three
+// Staple in two-row form (FP32 links, 12- or 18-real).  Each staple term is a product of three
 // SU(3) links, hence in SU(3): only rows 0, 1 of every partial product are
 // computed and row 2 is rebuilt, and a link that enters only through its rows
 // (the left factor) is never completed.
 //   up = (a b^+) c^+            a = U_nu(x+mu), b = U_mu(x+nu), c = U_nu(x)
 //   dn = (e d)^+ f              d = U_nu(x+mu-nu), e = U_mu(x-nu), f = U_nu(x-nu)
-template <class T>
-__device__ __forceinline__ M3<T> staple_two_row(const Links<T, 6>& U, const Geom& g, const int x[4], int h, int mu,
+template <class T, int NP>
+__device__ __forceinline__ M3<T> staple_two_row(const Links<T, NP>& U, const Geom& g, const int x[4], int h, int mu,
                                                 int par) {
     M3<T> A;
 #pragma unroll
@@ -97,7 +97,9 @@ __device__ __forceinline__ M3<T> staple_two_row(const Links<T, 6>& U, const Geom
 
 template <class T, int NP>
 __device__ __forceinline__ M3<T> staple(const Links<T, NP>& U, const Geom& g, const int x[4], int h, int mu, int par) {
-    if constexpr (NP == 6) {
+    if constexpr (sizeof(T) == 4) {
+        // FP32 (both formats): products of SU(3) factors in two-row form; the
+        // FP64 parity path below keeps full products in the oracle's order.
         return staple_two_row(U, g, x, h, mu, par);
     }
     M3<T> A;
@@ -170,6 +172,32 @@ __device__ __forceinline__ void su2_rows(M3<T>& m, int i, int j, const T r[4], b
         const Cx<T> mi = m.e[i][k], mj = m.e[j][k];
         if (do_i && ((ci >> k) & 1)) m.e[i][k] = a * mi + b * mj;
         if (do_j && ((cj >> k) & 1)) m.e[j][k] = c * mi + d * mj;
+    }
+}
+
+// FP32: a m_i + b m_j with a = r0 + i r3, b = r2 + i r1 (and c = -r2 + i r1,
+// d = r0 - i r3 for row j) as packed FMAs on (re, im) pairs.
+template <>
+__device__ __forceinline__ void su2_rows<float>(M3<float>& m, int i, int j, const float r[4], bool do_i, bool do_j,
+                                                int ci, int cj) {
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float2 MI = make_float2(m.e[i][k].re, m.e[i][k].im), iMI = make_float2(-m.e[i][k].im, m.e[i][k].re);
+        const float2 MJ = make_float2(m.e[j][k].re, m.e[j][k].im), iMJ = make_float2(-m.e[j][k].im, m.e[j][k].re);
+        if (do_i && ((ci >> k) & 1)) {
+            float2 v = __fmul2_rn(bcast(r[0]), MI);
+            v = __ffma2_rn(bcast(r[3]), iMI, v);
+            v = __ffma2_rn(bcast(r[2]), MJ, v);
+            v = __ffma2_rn(bcast(r[1]), iMJ, v);
+            m.e[i][k] = from_f2(v);
+        }
+        if (do_j && ((cj >> k) & 1)) {
+            float2 v = __fmul2_rn(bcast(-r[2]), MI);
+            v = __ffma2_rn(bcast(r[1]), iMI, v);
+            v = __ffma2_rn(bcast(r[0]), MJ, v);
+            v = __ffma2_rn(bcast(-r[3]), iMJ, v);
+            m.e[j][k] = from_f2(v);
+        }
     }
 }
 
