@@ -231,11 +231,16 @@ template <> __device__ __forceinline__ void rebuild_row2<float>(M3<float>& u) {
     }
 }
 
+// 1/sqrt(n): the correctly rounded quotient in FP64 (the oracle's operations),
+// the hardware reciprocal square root in FP32.
+__device__ __forceinline__ double inv_norm(double n) { return 1.0 / sqrt(n); }
+__device__ __forceinline__ float inv_norm(float n) { return rsqrtf(n); }
+
 // Gram-Schmidt reunitarisation: normalise row 0, orthogonalise and
 // normalise row 1, rebuild row 2 (determinant one).
 template <class T> __device__ __forceinline__ void reunitarize(M3<T>& u) {
     T n0 = norm2(u.e[0][0]) + norm2(u.e[0][1]) + norm2(u.e[0][2]);
-    T inv0 = T(1) / m_sqrt(n0);
+    T inv0 = inv_norm(n0);
 #pragma unroll
     for (int k = 0; k < 3; k++) u.e[0][k] = scale(u.e[0][k], inv0);
     // <r0, row1> = sum conj(r0_k) row1_k
@@ -243,7 +248,7 @@ template <class T> __device__ __forceinline__ void reunitarize(M3<T>& u) {
 #pragma unroll
     for (int k = 0; k < 3; k++) u.e[1][k] = u.e[1][k] - ip * u.e[0][k];
     T n1 = norm2(u.e[1][0]) + norm2(u.e[1][1]) + norm2(u.e[1][2]);
-    T inv1 = T(1) / m_sqrt(n1);
+    T inv1 = inv_norm(n1);
 #pragma unroll
     for (int k = 0; k < 3; k++) u.e[1][k] = scale(u.e[1][k], inv1);
     rebuild_row2(u);
@@ -388,8 +393,9 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
             k.x += 0x9E3779B9u;
             k.y += 0xBB67AE85u;
         }
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
         c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
     }
     return c;

@@ -225,8 +225,12 @@ __device__ __forceinline__ void apply_subgroup(M3<T>& u, M3<T>& v, int s, const 
 __device__ __forceinline__ double creutz_a0(double k, double em, double u0) { return 1.0 + log1p((1.0 - u0) * em) / k; }
 __device__ __forceinline__ float creutz_a0(float k, float em, float u0) {
     const float y = (1.f - u0) * em;
-    return 1.f + (y < -0.1f ? __logf(1.f + y) : log1pf(y)) / k;
+    return 1.f + (y < -0.1f ? __logf(1.f + y) : log1pf(y)) * __frcp_rn(k);
 }
+__device__ __forceinline__ double creutz_k(double beta, double xi) { return 2.0 * beta * xi / 3.0; }
+__device__ __forceinline__ float creutz_k(float beta, float xi) { return xi * (beta * 0.666666667f); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double creutz_em(double k) { return expm1(-2.0 * k); }
 __device__ __forceinline__ float creutz_em(float k) { return k > 0.25f ? __expf(-2.f * k) - 1.f : expm1f(-2.f * k); }
 __device__ __forceinline__ void creutz_phi(double u3, double* s, double* c) { sincospi(2.0 * u3, s, c); }
@@ -256,7 +260,7 @@ __device__ __forceinline__ void hb_link(M3<T>& u, const M3<T>& A, T beta, int n_
         const T xi = m_sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
         uint8_t d = 255;
         if (xi >= tiny_norm<T>()) {
-            const T k = T(2) * beta * xi / T(3);
+            const T k = creutz_k(beta, xi);
             const T em = creutz_em(k);
             for (int att = 0; att < n_hb; att++) {
                 const uint4 r = draw(rk, lex, mu, (uint32_t)s, (uint32_t)att, KIND_HB);
@@ -270,7 +274,7 @@ __device__ __forceinline__ void hb_link(M3<T>& u, const M3<T>& A, T beta, int n_
                     T sp, cp;
                     creutz_phi(u3, &sp, &cp);
                     const T X[4] = {a0, rad * st * cp, rad * st * sp, rad * ct};
-                    const T inv = T(1) / xi;
+                    const T inv = recip(xi);
                     const T wh[4] = {w[0] * inv, w[1] * inv, w[2] * inv, w[3] * inv};
                     T R[4];
                     qmul(X, wh, R);
@@ -296,7 +300,7 @@ __device__ __forceinline__ void or_link(M3<T>& u, const M3<T>& A) {
         block_w(v, i, j, w);
         const T n2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + w[3] * w[3];
         if (!(m_sqrt(n2) >= tiny_norm<T>())) continue;
-        const T inv2 = T(1) / n2;
+        const T inv2 = recip(n2);
         // (w/|w|)^2 = (w0^2 - |w_vec|^2, 2 w0 w_vec) / |w|^2
         const T R[4] = {(w[0] * w[0] - w[1] * w[1] - w[2] * w[2] - w[3] * w[3]) * inv2, T(2) * w[0] * w[1] * inv2,
                         T(2) * w[0] * w[2] * inv2, T(2) * w[0] * w[3] * inv2};
