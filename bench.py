@@ -163,19 +163,31 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
-def src_hash() -> str:
+# source files each profiled kernel is compiled from (shared headers + its .cu)
+KERNEL_SOURCES = {
+    "k_overrelax": "mgq_core.cu",
+    "k_heatbath": "mgq_core.cu",
+    "k_force": "mgq_hmc.cu",
+}
+_COMMON = ["mgq_device.cuh", "mgq_stencil.cuh", "mgq_internal.h"]
+
+
+def src_hash(kernel: str) -> str:
+    """Hash of the sources a kernel is compiled from; a profile summary whose
+    hash differs was taken on other code."""
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_1510_04675_gb300", "csrc", "*")) +
-                   glob.glob(os.path.join(ROOT, "include", "*.h")))
-    for f in files:
-        h.update(open(f, "rb").read())
+    csrc = os.path.join(ROOT, "paper_1510_04675_gb300", "csrc")
+    for f in _COMMON + [KERNEL_SOURCES[kernel]]:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def traffic_from_profiles(kernel: str, workload_tag: str):
     """DRAM bytes per launch recorded by an ncu capture summary under profiles/,
-    if it was taken on the current kernel sources."""
-    cur = src_hash()
+    if it was taken on the current sources of that kernel."""
+    if kernel not in KERNEL_SOURCES:
+        return None
+    cur = src_hash(kernel)
     for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.txt"))):
         for line in open(f):
             t = line.split()

@@ -101,6 +101,18 @@ uint64_t mgq_links_bytes(const mgq_lattice* lat);
 uint64_t mgq_mom_bytes(const mgq_lattice* lat);
 uint64_t mgq_workspace_bytes(const mgq_lattice* lat);
 
+/* ---- launch tuning ------------------------------------------------------------
+ * Threads per block of the checkerboard sub-sweep kernels (heat bath and
+ * overrelaxation) of the single-lattice entry points, per
+ * storage format: 32, 64, 96 or 128 (the kernels are compiled for at most
+ * 128); 128 by default.  Results do not depend on it (one thread per link).
+ * Process-wide setting; change it only while no call is being issued.  Set
+ * by the autotuner (paper_1510_04675_gb300/tune.py). */
+typedef enum { MGQ_KERNEL_HEATBATH = 0, MGQ_KERNEL_OVERRELAX = 1 } mgq_kernel;
+mgq_status mgq_set_block_size(int kernel, int prec, int threads);
+/* Current value, 0 for an unknown kernel or precision. */
+int mgq_get_block_size(int kernel, int prec);
+
 /* ---- fields ---------------------------------------------------------------- */
 /* Start configurations (Sec. IV.E): start = 0 cold (unit links, the ordered
  * delta-function start), start = 1 hot (Haar-random SU(3) per link from the
@@ -185,6 +197,20 @@ mgq_status mgq_plaquette(const mgq_lattice* lat, double* plaq_out, void* stream)
  * streams, or other host threads on the same device -- race and must be
  * serialised by the caller.  plaq_out: one double, host or device. */
 mgq_status mgq_plaquette_noalloc(const mgq_lattice* lat, double* plaq_out, void* stream);
+
+/* Space-time averaged m x n Wilson loop (Sec. III):
+ * (1/(6V)) sum_x sum_{mu<nu} (1/3) Re Tr L^m_mu(x) L^n_nu(x+m mu)
+ * L^m_mu(x+n nu)^+ L^n_nu(x)^+, with the Wilson lines L^m_mu the ordered
+ * products of m links; 1 <= m, n <= 64.  out: one double, host or device. */
+mgq_status mgq_wilson_loop(const mgq_lattice* lat, int m, int n, double* out, void* stream);
+
+/* Rethermalisation diagnostics (Sec. III, IV.C, IV.E), nine doubles (host or
+ * device): out[0..2] partial plaquettes W^{1x1}_d (plaquettes with
+ * chi_munu(n) = d, normalised by N^{1x1}_d = 2 (D-d)(D-d-1) C(D,d) N_0/2^D),
+ * out[3..7] displaced loops W^{2x2}_d (2x2 loops from sites with chi(n) = d,
+ * N^{2x2}_d = C(D,2) C(D,d) N_0/2^D), out[8] h = max_p N_c [1 - W^{1x1}_p]
+ * (admissibility when h < 0.067). */
+mgq_status mgq_partial_loops(const mgq_lattice* lat, double* out, void* stream);
 
 /* Clover energy density E = (1/V) sum_x -1/2 sum_{mu,nu} Tr G_munu^2 and
  * charge Q = -1/(32 pi^2) sum_x eps_{munurhosigma} Tr G_munu G_rhosigma,

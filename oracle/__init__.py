@@ -76,6 +76,8 @@ _SIGS = {
     "orc_partial_action": (_dbl, [_D, _I, _int]),
     "orc_prolongate": (None, [_D, _I, _D, _dbl, _dbl, _int, _int, _I, _D]),
     "orc_flow_step": (None, [_D, _I, _dbl]),
+    "orc_wilson_loop": (_dbl, [_D, _I, _int, _int]),
+    "orc_partial_loops": (None, [_D, _I, _D]),
     "orc_clover_EQ": (None, [_D, _I, _D, _D]),
     "orc_wilson_flow": (None, [_D, _I, _dbl, _int, _int, _D, _D]),
     "orc_set_threads": (None, [_int]),
@@ -360,3 +362,15 @@ def wilson_flow(W, dims, eps, n_steps, meas_every):
     lib().orc_wilson_flow(_dp(W.view(np.float64)), _dims(dims), float(eps), int(n_steps), int(meas_every),
                           _dp(E), _dp(Q))
     return E, Q
+
+
+# ---------------------------------------------------------------- loops
+def wilson_loop(U, dims, m, n) -> float:
+    return float(lib().orc_wilson_loop(_dp(U.view(np.float64)), _dims(dims), int(m), int(n)))
+
+
+def partial_loops(U, dims) -> np.ndarray:
+    """[W1x1_0..2, W2x2_0..4, h] (see orc_partial_loops)."""
+    out = np.zeros(9)
+    lib().orc_partial_loops(_dp(U.view(np.float64)), _dims(dims), _dp(out))
+    return out

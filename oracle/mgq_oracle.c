@@ -1046,6 +1046,105 @@ void orc_prolongate(const double* Uc, const int* dims_c, double* Uf, double c, d
 }
 
 /* ------------------------------------------------------------------------ */
+/* Wilson loops and the rethermalisation diagnostics (Sec. III: Wilson      */
+/* lines, m x n loops, partial plaquettes, displaced 2x2 loops; Sec. IV.C:  */
+/* smoothness s_p and admissibility).                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Wilson line L^m_mu(x) = U_mu(x) U_mu(x+mu) ... U_mu(x+(m-1)mu) */
+static mat3 wilson_line(const lat_t* g, const double* U, long s, int mu, int m)
+{
+    mat3 L = m_unit();
+    for (int k = 0; k < m; k++) {
+        L = m_mul(L, getU(U, s, mu));
+        s = hop(g, s, mu, +1);
+    }
+    return L;
+}
+
+/* W^{m x n}_munu(x) = (1/3) Re Tr L^m_mu(x) L^n_nu(x+m mu) L^m_mu(x+n nu)^+ L^n_nu(x)^+ */
+static double loop_mn(const lat_t* g, const double* U, long s, int mu, int nu, int m, int n)
+{
+    long xm = s, xn = s;
+    for (int k = 0; k < m; k++) xm = hop(g, xm, mu, +1);
+    for (int k = 0; k < n; k++) xn = hop(g, xn, nu, +1);
+    mat3 a = m_mul(wilson_line(g, U, s, mu, m), wilson_line(g, U, xm, nu, n));
+    mat3 b = m_mul(wilson_line(g, U, s, nu, n), wilson_line(g, U, xn, mu, m));
+    return creal(m_trace(m_mul(a, m_dag(b)))) / 3.0;
+}
+
+/* Space-time average of the m x n loops over all x and mu < nu, normalised by N_2 = 6 V. */
+double orc_wilson_loop(const double* U, const int* dims, int m, int n)
+{
+    lat_t g = make_lat(dims);
+    double* part = malloc(sizeof(double) * g.V);
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < g.V; s++) {
+        double acc = 0;
+        for (int mu = 0; mu < 4; mu++)
+            for (int nu = mu + 1; nu < 4; nu++) acc += loop_mn(&g, U, s, mu, nu, m, n);
+        part[s] = acc;
+    }
+    double acc = 0;
+    for (long s = 0; s < g.V; s++) acc += part[s];
+    free(part);
+    return acc / (6.0 * (double)g.V);
+}
+
+static double binom(int n, int k)
+{
+    double r = 1;
+    for (int i = 1; i <= k; i++) r = r * (n - k + i) / i;
+    return r;
+}
+
+/*
+ * out[0..2]: partial plaquettes W^{1x1}_d = (1/N^{1x1}_d) sum over plaquettes
+ *            with chi_munu(n) = d of W^{1x1}_munu(n),
+ *            N^{1x1}_d = 2 (D-d)(D-d-1) C(D,d) N_0 / 2^D;
+ * out[3..7]: displaced loops W^{2x2}_d = (1/N^{2x2}_d) sum over (n, mu<nu)
+ *            with chi(n) = d of W^{2x2}_munu(n), N^{2x2}_d = C(D,2) C(D,d) N_0 / 2^D;
+ * out[8]   : h = max_p s_p, s_p = N_c [1 - W^{1x1}_p].
+ * Defined for lattices with even extents; the d classes refer to the coarse
+ * lattice of the even sites.
+ */
+void orc_partial_loops(const double* U, const int* dims, double* out)
+{
+    lat_t g = make_lat(dims);
+    const int D = 4;
+    double* p1 = calloc((size_t)g.V * 3, sizeof(double));
+    double* p2 = calloc((size_t)g.V * 5, sizeof(double));
+    double* hx = calloc((size_t)g.V, sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < g.V; s++) {
+        int x[4];
+        coords_of(&g, s, x);
+        int chi = 0;
+        for (int r = 0; r < 4; r++) chi += x[r] & 1;
+        double hmax = 0;
+        for (int mu = 0; mu < 4; mu++)
+            for (int nu = mu + 1; nu < 4; nu++) {
+                double w1 = loop_mn(&g, U, s, mu, nu, 1, 1);
+                p1[(size_t)s * 3 + chi_munu(x, mu, nu)] += w1;
+                p2[(size_t)s * 5 + chi] += loop_mn(&g, U, s, mu, nu, 2, 2);
+                double sp = 3.0 * (1.0 - w1);
+                if (sp > hmax) hmax = sp;
+            }
+        hx[s] = hmax;
+    }
+    double a1[3] = {0, 0, 0}, a2[5] = {0, 0, 0, 0, 0}, h = 0;
+    for (long s = 0; s < g.V; s++) {
+        for (int d = 0; d < 3; d++) a1[d] += p1[(size_t)s * 3 + d];
+        for (int d = 0; d < 5; d++) a2[d] += p2[(size_t)s * 5 + d];
+        if (hx[s] > h) h = hx[s];
+    }
+    for (int d = 0; d < 3; d++) out[d] = a1[d] / (2.0 * (D - d) * (D - d - 1) * binom(D, d) * (double)g.V / 16.0);
+    for (int d = 0; d < 5; d++) out[3 + d] = a2[d] / (binom(D, 2) * binom(D, d) * (double)g.V / 16.0);
+    out[8] = h;
+    free(p1); free(p2); free(hx);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Wilson flow (Sec. IV.B, fixed step, Luscher's third-order Runge-Kutta)    */
 /* and clover observables E(t), Q(t).                                        */
 /* ------------------------------------------------------------------------ */

@@ -12,6 +12,7 @@ LIB_PATH = os.path.join(PKG, "libmgq.so")
 MGQ_OK, MGQ_EINVAL, MGQ_ENOMEM, MGQ_ECUDA, MGQ_EUNSUPPORTED, MGQ_ETIMEOUT, MGQ_ENONUNITARY = range(7)
 MGQ_F64, MGQ_F32, MGQ_F32_C12 = 0, 1, 2
 MGQ_WILSON = 0
+MGQ_KERNEL_HEATBATH, MGQ_KERNEL_OVERRELAX = 0, 1
 MGQ_PERIODIC, MGQ_OPEN = 0, 1
 
 
@@ -60,6 +61,8 @@ SIGNATURES = {
     "mgq_plaquette": (_st, [_P, _vp, _vp]),
     "mgq_plaquette_noalloc": (_st, [_P, _vp, _vp]),
     "mgq_topo_charge": (_st, [_P, _vp, _vp, _vp]),
+    "mgq_wilson_loop": (_st, [_P, _i, _i, _vp, _vp]),
+    "mgq_partial_loops": (_st, [_P, _vp, _vp]),
     "mgq_wilson_flow": (_st, [_P, _d, _i, _i, _vp, _vp, _vp]),
     "mgq_hmc_force": (_st, [_P, _d, _vp, _vp]),
     "mgq_link_exp_update": (_st, [_P, _vp, _d, _vp]),
@@ -71,6 +74,8 @@ SIGNATURES = {
     "mgq_restrict": (_st, [_P, _P, _vp]),
     "mgq_check_unitarity": (_st, [_P, _d, _vp, _vp]),
     "mgq_batch_workspace_bytes": (ctypes.c_uint64, [_P, _i, _i]),
+    "mgq_set_block_size": (_st, [_i, _i, _i]),
+    "mgq_get_block_size": (ctypes.c_int, [_i, _i]),
     "mgq_update_sweeps_batched": (_st, [_P, _i, ctypes.POINTER(ctypes.c_double), _u64, _i, _i, _i, _vp, _vp, _u64,
                                         _vp]),
 }

@@ -324,3 +324,17 @@ def mgq_wilson_flow_step_adjoint(lat: Lattice, eps: float, lam: torch.Tensor, sc
     """Pull a cotangent back through one RK3 flow step that starts at the lattice's links."""
     call("mgq_wilson_flow_step_adjoint", lat.ref, float(eps), _ptr(lam), _ptr(scratch), int(scratch.numel()),
          _stream_handle(stream))
+
+
+# ------------------------------------------------------------------ loops
+def mgq_wilson_loop(lat: Lattice, m: int, n: int, stream=None) -> float:
+    v = ctypes.c_double()
+    call("mgq_wilson_loop", lat.ref, int(m), int(n), ctypes.byref(v), _stream_handle(stream))
+    return float(v.value)
+
+
+def mgq_partial_loops(lat: Lattice, stream=None) -> np.ndarray:
+    """[W1x1_0..2, W2x2_0..4, h] as float64."""
+    out = np.zeros(9)
+    call("mgq_partial_loops", lat.ref, ctypes.c_void_p(out.ctypes.data), _stream_handle(stream))
+    return out

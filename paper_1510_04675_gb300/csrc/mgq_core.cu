@@ -308,13 +308,19 @@ __global__ void k_final_max(const double* __restrict__ partials, int n, double* 
 // =============================================================== launchers
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
+// Launch shape of the sub-sweep kernels per (kernel, precision): threads per
+// block, at most the 128 the kernels are compiled for.  Set by
+// mgq_set_block_size (the autotuner); 128 by default.
+static int g_block[2][3] = {{128, 128, 128}, {128, 128, 128}};
+
 mgq_status heatbath_subsweep(mgq_lattice* lat, double beta, uint64_t sweep, int n_hb, int mu, int par,
                              uint8_t* dec, cudaStream_t st) {
     const Geom g = make_geom(lat->dims);
+    const int bs = g_block[MGQ_KERNEL_HEATBATH][lat->prec];
     const RngKey rk = make_rng(lat->seed, lat->lattice_id, sweep);
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
         dispatch_mu(mu, [&]<int MU>() {
-            k_heatbath<T, NP, MU><<<nblk(g.Vh, 128), 128, 0, st>>>(links_of<T, NP>(lat), g, par, (T)beta, rk, n_hb, dec);
+            k_heatbath<T, NP, MU><<<nblk(g.Vh, bs), bs, 0, st>>>(links_of<T, NP>(lat), g, par, (T)beta, rk, n_hb, dec);
         });
     });
     return cuda_check("mgq_heatbath");
@@ -322,9 +328,10 @@ mgq_status heatbath_subsweep(mgq_lattice* lat, double beta, uint64_t sweep, int 
 
 mgq_status overrelax_subsweep(mgq_lattice* lat, int mu, int par, cudaStream_t st) {
     const Geom g = make_geom(lat->dims);
+    const int bs = g_block[MGQ_KERNEL_OVERRELAX][lat->prec];
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
         dispatch_mu(mu, [&]<int MU>() {
-            k_overrelax<T, NP, MU><<<nblk(g.Vh, 128), 128, 0, st>>>(links_of<T, NP>(lat), g, par);
+            k_overrelax<T, NP, MU><<<nblk(g.Vh, bs), bs, 0, st>>>(links_of<T, NP>(lat), g, par);
         });
     });
     return cuda_check("mgq_overrelax");
@@ -369,6 +376,20 @@ uint64_t mgq_site_stride(const int32_t dims[4]) { return site_stride(dims); }
 uint64_t mgq_links_bytes(const mgq_lattice* lat) { return links_bytes(lat); }
 uint64_t mgq_mom_bytes(const mgq_lattice* lat) { return alg_bytes(lat); }
 uint64_t mgq_workspace_bytes(const mgq_lattice* lat) { return workspace_bytes(lat); }
+
+mgq_status mgq_set_block_size(int kernel, int prec, int threads) {
+    if (kernel < 0 || kernel > 1) return fail(MGQ_EINVAL, "mgq_set_block_size: unknown kernel %d", kernel);
+    if (prec < MGQ_F64 || prec > MGQ_F32_C12) return fail(MGQ_EINVAL, "mgq_set_block_size: prec %d invalid", prec);
+    if (threads < 32 || threads > 128 || (threads & 31))
+        return fail(MGQ_EINVAL, "mgq_set_block_size: threads must be 32, 64, 96 or 128");
+    g_block[kernel][prec] = threads;
+    return MGQ_OK;
+}
+
+int mgq_get_block_size(int kernel, int prec) {
+    if (kernel < 0 || kernel > 1 || prec < MGQ_F64 || prec > MGQ_F32_C12) return 0;
+    return g_block[kernel][prec];
+}
 
 mgq_status mgq_init_links(mgq_lattice* lat, int start, void* stream) {
     mgq_status s = check_lattice(lat, false, "mgq_init_links");

@@ -425,7 +425,9 @@ __device__ __forceinline__ uint4 draw(const RngKey& k, uint32_t lex, uint32_t mu
 template <class T> __device__ __forceinline__ T u01(uint32_t w);
 template <> __device__ __forceinline__ double u01<double>(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
 template <> __device__ __forceinline__ float u01<float>(uint32_t w) {
-    return __uint2float_rn(w >> 9) * 0x1p-23f + 0x1p-24f;
+    // 1 + m 2^-23 built from the bits, minus (1 - 2^-24): exact (Sterbenz),
+    // equal to (m + 1/2) 2^-23 with m = w >> 9, without an int-to-float conversion
+    return __int_as_float(0x3f800000u | (w >> 9)) - 0x1.fffffep-1f;
 }
 
 // ----------------------------------------------------------------- su(3)

@@ -231,6 +231,10 @@ __device__ __forceinline__ double creutz_k(double beta, double xi) { return 2.0 
 __device__ __forceinline__ float creutz_k(float beta, float xi) { return xi * (beta * 0.666666667f); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+// sqrt of a positive argument (both uses above are > 0: rest >= u1^2 > 0 and
+// |cos theta| < 1); FP32 takes x rsqrt(x)
+__device__ __forceinline__ double sampler_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float sampler_sqrt(float x) { return x * rsqrtf(x); }
 __device__ __forceinline__ double creutz_em(double k) { return expm1(-2.0 * k); }
 __device__ __forceinline__ float creutz_em(float k) { return k > 0.25f ? __expf(-2.f * k) - 1.f : expm1f(-2.f * k); }
 __device__ __forceinline__ void creutz_phi(double u3, double* s, double* c) { sincospi(2.0 * u3, s, c); }
@@ -268,9 +272,9 @@ __device__ __forceinline__ void hb_link(M3<T>& u, const M3<T>& A, T beta, int n_
                 const T a0 = creutz_a0(k, em, u0);
                 const T rest = sub_rn(T(1), mul_rn(a0, a0));
                 if (mul_rn(u1, u1) <= rest) {
-                    const T rad = m_sqrt(rest);
+                    const T rad = sampler_sqrt(rest);
                     const T ct = T(2) * u2 - T(1);
-                    const T st = m_sqrt(sub_rn(T(1), mul_rn(ct, ct)));
+                    const T st = sampler_sqrt(sub_rn(T(1), mul_rn(ct, ct)));
                     T sp, cp;
                     creutz_phi(u3, &sp, &cp);
                     const T X[4] = {a0, rad * st * cp, rad * st * sp, rad * ct};

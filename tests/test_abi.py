@@ -91,3 +91,12 @@ def test_argument_ranges(mgqlib):
     assert mgqlib.mgq_plaquette(ctypes.byref(c), ctypes.c_void_p(1 << 21), None) == 2
     assert mgqlib.mgq_abi_version() == 1
     assert mgqlib.mgq_status_string(2) == b"workspace too small"
+
+
+def test_block_size_settings(mgqlib):
+    assert mgqlib.mgq_get_block_size(0, 2) == 128
+    assert mgqlib.mgq_set_block_size(0, 2, 64) == 0 and mgqlib.mgq_get_block_size(0, 2) == 64
+    assert mgqlib.mgq_set_block_size(0, 2, 128) == 0
+    for bad in [(0, 2, 48), (0, 2, 256), (2, 0, 64), (1, 5, 64)]:
+        assert mgqlib.mgq_set_block_size(*bad) == 1
+    assert mgqlib.mgq_get_block_size(7, 0) == 0
