@@ -59,6 +59,7 @@ _SIGS = {
     "orc_overrelax_sweep": (None, [_D, _I]),
     "orc_overrelax_one_link": (None, [_D, _I, _long, _int, _D]),
     "orc_overrelax_subsweep": (None, [_D, _I, _int, _int]),
+    "orc_subsweep_range": (None, [_D, _I, _int, _dbl, _u64, _u32, _u64, _int, _int, _int, _long, _long]),
     "orc_update_chain": (None, [_D, _I, _dbl, _u64, _u32, _u64, _int, _int, _int, _D]),
     "orc_expm": (None, [_D, _D]),
     "orc_alg_to_mat": (None, [_D, _D]),
@@ -227,6 +228,12 @@ def overrelax_sweep(U, dims):
 
 def overrelax_subsweep(U, dims, mu, parity):
     lib().orc_overrelax_subsweep(_dp(U.view(np.float64)), _dims(dims), int(mu), int(parity))
+
+
+def subsweep_range(U, dims, kind, beta, seed, lattice_id, sweep, n_hb, mu, parity, s_lo, s_hi):
+    """(mu, parity) heat-bath (kind 0) or overrelaxation (kind 1) updates of the sites in [s_lo, s_hi)."""
+    lib().orc_subsweep_range(_dp(U.view(np.float64)), _dims(dims), int(kind), float(beta), seed, lattice_id, sweep,
+                             int(n_hb), int(mu), int(parity), int(s_lo), int(s_hi))
 
 
 def overrelax_one_link(U, dims, s, mu):

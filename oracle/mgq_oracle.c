@@ -614,6 +614,27 @@ void orc_overrelax_sweep(double* U, const int* dims)
         }
 }
 
+/*
+ * The same (mu, parity) updates restricted to the sites with lexicographic
+ * index in [s_lo, s_hi) (a slab of x3 planes when the bounds are multiples of
+ * L0 L1 L2); used to time bounded samples of a sweep.  kind 0 = heat bath,
+ * 1 = overrelaxation.
+ */
+void orc_subsweep_range(double* U, const int* dims, int kind, double beta, uint64_t seed, uint32_t lattice_id,
+                        uint64_t sweep, int n_hb, int mu, int par, long s_lo, long s_hi)
+{
+    lat_t g = make_lat(dims);
+#pragma omp parallel for schedule(static)
+    for (long s = s_lo; s < s_hi; s++) {
+        if (parity_of(&g, s) != par) continue;
+        uint8_t d[3];
+        mat3 A = staple(&g, U, s, mu);
+        mat3 Un = kind == 0 ? hb_link(getU(U, s, mu), A, beta, n_hb, seed, lattice_id, s, mu, sweep, d)
+                            : or_link(getU(U, s, mu), A);
+        setU(U, s, mu, Un);
+    }
+}
+
 /* One (mu, parity) subset of the overrelaxation sweep. */
 void orc_overrelax_subsweep(double* U, const int* dims, int mu, int par)
 {
