@@ -249,6 +249,18 @@ mgq_status mgq_flow_vjp(const mgq_lattice* lat, const void* psi, double scale, v
 mgq_status mgq_wilson_flow_step_adjoint(const mgq_lattice* lat, double eps, void* lambda, void* scratch,
                                         uint64_t scratch_bytes, void* stream);
 
+/* Bytes of the caller scratch of mgq_clover_vjp (6 planes x 8 reals per site). */
+uint64_t mgq_clover_vjp_scratch_bytes(const mgq_lattice* lat);
+
+/* lambda += scale * dO/de: the gradient of the clover observable O
+ * (observable 0: E, 1: Q, as in mgq_topo_charge) with respect to the links
+ * at lat->links, as a cotangent (mom layout and precision, device).  This is
+ * the starting cotangent of the backward pass of a flowed clover observable.
+ * scratch: device, 256-B aligned, >= mgq_clover_vjp_scratch_bytes.
+ * Errors: MGQ_EINVAL, MGQ_ENOMEM. */
+mgq_status mgq_clover_vjp(const mgq_lattice* lat, int observable, double scale, void* lambda, void* scratch,
+                          uint64_t scratch_bytes, void* stream);
+
 /* ---- HMC (Sec. IV.D, App. A) ------------------------------------------------- */
 
 /* Gauge force F(x,mu) = -(beta/6) TA(U_mu(x) A_mu(x)) into force_out

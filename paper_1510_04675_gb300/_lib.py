@@ -69,6 +69,8 @@ SIGNATURES = {
     "mgq_flow_adjoint_scratch_bytes": (ctypes.c_uint64, [_P]),
     "mgq_flow_vjp": (_st, [_P, _vp, _d, _vp, _vp]),
     "mgq_wilson_flow_step_adjoint": (_st, [_P, _d, _vp, _vp, _u64, _vp]),
+    "mgq_clover_vjp_scratch_bytes": (ctypes.c_uint64, [_P]),
+    "mgq_clover_vjp": (_st, [_P, _i, _d, _vp, _vp, _u64, _vp]),
     "mgq_hmc_trajectory": (_st, [_P, _d, _d, _i, _u64, _i, _vp, _vp, _vp]),
     "mgq_prolongate": (_st, [_P, _P, _d, _d, _i, _vp, _vp, _vp]),
     "mgq_restrict": (_st, [_P, _P, _vp]),

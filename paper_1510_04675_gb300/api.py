@@ -338,3 +338,11 @@ def mgq_partial_loops(lat: Lattice, stream=None) -> np.ndarray:
     out = np.zeros(9)
     call("mgq_partial_loops", lat.ref, ctypes.c_void_p(out.ctypes.data), _stream_handle(stream))
     return out
+
+
+def mgq_clover_vjp(lat: Lattice, observable: str, scale: float, lam: torch.Tensor, stream=None) -> None:
+    """lam += scale * gradient of the clover observable ("E" or "Q") at the lattice's links."""
+    n = int(_lib.load().mgq_clover_vjp_scratch_bytes(lat.ref))
+    scratch = torch.empty(n, dtype=torch.uint8, device=lat.device)
+    call("mgq_clover_vjp", lat.ref, {"E": 0, "Q": 1}[observable], float(scale), _ptr(lam), _ptr(scratch), n,
+         _stream_handle(stream))

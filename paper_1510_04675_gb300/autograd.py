@@ -39,20 +39,23 @@ def wilson_action(omega: torch.Tensor, lat: "api.Lattice", beta: float) -> torch
     return WilsonAction.apply(omega, lat, beta)
 
 
-class FlowedWilsonAction(torch.autograd.Function):
-    """L(omega) = S_W(W_t), W_t the Wilson flow (n_steps fixed steps of size eps,
-    Sec. IV.B) of exp(omega) U.
+class FlowedObservable(torch.autograd.Function):
+    """L(omega) = O(W_t), W_t the Wilson flow (n_steps fixed steps of size eps,
+    Sec. IV.B) of exp(omega) U, O one of
+      "S": the Wilson action at coupling beta,
+      "E": the clover energy density, "Q": the clover topological charge.
 
     Forward: the flow kernels, keeping a copy of the field every
-    `checkpoint_every` steps.  Backward: the cotangent -F(W_t) (force kernel)
-    is pulled back step by step with the adjoint-flow kernels
+    `checkpoint_every` steps (default sqrt(n_steps)).  Backward: the gradient
+    of O at W_t -- the force kernel for S, mgq_clover_vjp for E and Q -- is
+    pulled back step by step with the adjoint-flow kernels
     (mgq_wilson_flow_step_adjoint); each segment between checkpoints is
     recomputed forward to recover the start of every step.  Memory: the
     checkpoints plus one segment of link fields.
     """
 
     @staticmethod
-    def forward(ctx, omega, lat, beta, eps, n_steps, checkpoint_every=None):
+    def forward(ctx, omega, lat, observable, eps, n_steps, beta=6.0, checkpoint_every=None):
         import math
 
         k = int(checkpoint_every or max(1, int(math.isqrt(max(1, n_steps)))))
@@ -65,20 +68,28 @@ class FlowedWilsonAction(torch.autograd.Function):
             m = min(k, n_steps - done)
             api.mgq_wilson_flow(W, eps, m, m)
             done += m
-        plaq = api.mgq_plaquette(W)
-        ctx.W, ctx.ckpts, ctx.beta, ctx.eps, ctx.n = W, ckpts, float(beta), float(eps), int(n_steps)
-        return torch.tensor(float(beta) * 6.0 * W.volume * (1.0 - plaq), dtype=torch.float64, device=omega.device)
+        if observable == "S":
+            value = float(beta) * 6.0 * W.volume * (1.0 - api.mgq_plaquette(W))
+        else:
+            E, Q = api.mgq_topo_charge(W)
+            value = E if observable == "E" else Q
+        ctx.W, ctx.ckpts, ctx.k = W, ckpts, k
+        ctx.obs, ctx.beta, ctx.eps, ctx.n = observable, float(beta), float(eps), int(n_steps)
+        return torch.tensor(value, dtype=torch.float64, device=omega.device)
 
     @staticmethod
     def backward(ctx, grad_L):
         W = ctx.W
         lam = W.new_alg_field()
-        api.mgq_hmc_force(W, ctx.beta, lam)      # F = -dS/domega at W_t
-        lam.mul_(-1.0)
+        if ctx.obs == "S":
+            api.mgq_hmc_force(W, ctx.beta, lam)      # F = -dS/domega at W_t
+            lam.mul_(-1.0)
+        else:
+            api.mgq_clover_vjp(W, ctx.obs, 1.0, lam)
         scratch = api.flow_adjoint_scratch(W)
         seg = api.copy_lattice(W)
         for start, links in reversed(ctx.ckpts):
-            m = min(ctx.n - start, (ctx.ckpts[1][0] - ctx.ckpts[0][0]) if len(ctx.ckpts) > 1 else ctx.n)
+            m = min(ctx.n - start, ctx.k)
             seg.links.copy_(links)
             starts = []
             for _ in range(m):
@@ -87,8 +98,13 @@ class FlowedWilsonAction(torch.autograd.Function):
             for w0 in reversed(starts):
                 seg.links.copy_(w0)
                 api.mgq_wilson_flow_step_adjoint(seg, ctx.eps, lam, scratch)
-        return (lam.double() * grad_L).to(lam.dtype), None, None, None, None, None
+        return (lam.double() * grad_L).to(lam.dtype), None, None, None, None, None, None
+
+
+def flowed_observable(omega, lat, observable, eps, n_steps, beta=6.0, checkpoint_every=None):
+    """Differentiable O(W_t) for O in {"S", "E", "Q"} (see FlowedObservable)."""
+    return FlowedObservable.apply(omega, lat, observable, eps, n_steps, beta, checkpoint_every)
 
 
 def flowed_wilson_action(omega, lat, beta, eps, n_steps, checkpoint_every=None):
-    return FlowedWilsonAction.apply(omega, lat, beta, eps, n_steps, checkpoint_every)
+    return FlowedObservable.apply(omega, lat, "S", eps, n_steps, beta, checkpoint_every)

@@ -160,6 +160,43 @@ __device__ __forceinline__ double site_plaquettes(const Links<T, NP>& U, const G
     return acc;
 }
 
+// =============================================================== clover
+// Clover leaves around x in the (mu,nu) plane, all starting and ending at x,
+// counterclockwise; returns the algebra coefficients g of
+// G = traceless part of (Q - Q^+)/8, i.e. g = t(TA(Q))/4.
+template <class T, int NP>
+__device__ __forceinline__ void clover_coeffs(const Links<T, NP>& U, const Geom& g, const int x[4], int par, int h, int mu,
+                                              int nu, T out[8]) {
+    const int op = par ^ 1;
+    const int lpm = lex_hop(g, x, mu, +1), lpn = lex_hop(g, x, nu, +1);
+    const int lmm = lex_hop(g, x, mu, -1), lmn = lex_hop(g, x, nu, -1);
+    const int lmm_pn = lex_hop(g, x, mu, -1, nu, +1);
+    const int lmm_mn = lex_hop(g, x, mu, -1, nu, -1);
+    const int lpm_mn = lex_hop(g, x, mu, +1, nu, -1);
+    const M3<T> umu = U.load(mu, par, h), unu = U.load(nu, par, h);
+    // l1 = U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
+    M3<T> Q = mul_nd(mul_nn(umu, U.load(nu, op, lpm >> 1)), mul_nn(unu, U.load(mu, op, lpn >> 1)));
+    // l2 = U_nu(x) U_mu(x-mu+nu)^+ U_nu(x-mu)^+ U_mu(x-mu)
+    {
+        const M3<T> a = U.load(mu, par, lmm_pn >> 1), b = U.load(nu, op, lmm >> 1), c = U.load(mu, op, lmm >> 1);
+        acc_add(Q, mul_nn(mul_nd(unu, a), mul_dn(b, c)));
+    }
+    // l3 = U_mu(x-mu)^+ U_nu(x-mu-nu)^+ U_mu(x-mu-nu) U_nu(x-nu)
+    {
+        const M3<T> a = U.load(mu, op, lmm >> 1), b = U.load(nu, par, lmm_mn >> 1), c = U.load(mu, par, lmm_mn >> 1),
+                    d = U.load(nu, op, lmn >> 1);
+        acc_add(Q, mul_nn(mul_dd(a, b), mul_nn(c, d)));
+    }
+    // l4 = U_nu(x-nu)^+ U_mu(x-nu) U_nu(x+mu-nu) U_mu(x)^+
+    {
+        const M3<T> a = U.load(nu, op, lmn >> 1), b = U.load(mu, op, lmn >> 1), c = U.load(nu, par, lpm_mn >> 1);
+        acc_add(Q, mul_nd(mul_nn(mul_dn(a, b), c), umu));
+    }
+    ta_coeffs(Q, out);
+#pragma unroll
+    for (int a = 0; a < 8; a++) out[a] *= T(0.25);
+}
+
 // =============================================================== SU(2) steps
 // rows i, j of m <- R(r) rows i, j, restricted to the rows (do_i, do_j) and
 // columns (bit masks ci, cj) that are read later; with the subgroup index a

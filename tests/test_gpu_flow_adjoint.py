@@ -90,3 +90,33 @@ def test_checkpointed_flow_gradient(gpu, n_steps, every):
           - flowed_wilson_action(-h * v, lat, beta, eps, n_steps).item()) / (2 * h)
     ad = torch.dot(g, v).item()
     assert abs(fd - ad) < 1e-6 * max(1.0, abs(fd)), (fd, ad)
+
+
+@pytest.mark.parametrize("obs", ["E", "Q"])
+def test_clover_gradient(gpu, obs):
+    lat = _field(gpu, [4, 4, 4, 4], 21, sweeps=3)
+    lam = lat.new_alg_field()
+    gpu.mgq_clover_vjp(lat, obs, 1.0, lam)
+    gen = torch.Generator(device="cuda").manual_seed(22)
+    v = _rand_alg(lat, gen)
+    h = 1e-5
+    idx = 0 if obs == "E" else 1
+    fd = (gpu.mgq_topo_charge(_moved(gpu, lat, v, h))[idx] - gpu.mgq_topo_charge(_moved(gpu, lat, v, -h))[idx]) / (2 * h)
+    ad = torch.dot(lam, v).item()
+    assert abs(fd - ad) < 1e-6 * max(1e-3, abs(fd)), (fd, ad)
+
+
+@pytest.mark.parametrize("obs", ["E", "Q"])
+def test_flowed_clover_gradient(gpu, obs):
+    from paper_1510_04675_gb300.autograd import flowed_observable
+
+    lat = _field(gpu, [4, 4, 4, 4], 31, sweeps=3)
+    eps, n = 0.02, 8
+    omega = lat.new_alg_field().requires_grad_(True)
+    (g,) = torch.autograd.grad(flowed_observable(omega, lat, obs, eps, n, checkpoint_every=3), omega)
+    gen = torch.Generator(device="cuda").manual_seed(32)
+    v = _rand_alg(lat, gen)
+    h = 1e-5
+    fd = (flowed_observable(h * v, lat, obs, eps, n).item() - flowed_observable(-h * v, lat, obs, eps, n).item()) / (2 * h)
+    ad = torch.dot(g, v).item()
+    assert abs(fd - ad) < 1e-6 * max(1e-3, abs(fd)), (fd, ad)
