@@ -81,6 +81,8 @@ _SIGS = {
     "orc_partial_loops": (None, [_D, _I, _D]),
     "orc_clover_EQ": (None, [_D, _I, _D, _D]),
     "orc_wilson_flow": (None, [_D, _I, _dbl, _int, _int, _D, _D]),
+    "orc_flow_trial_step": (_dbl, [_D, _I, _dbl]),
+    "orc_wilson_flow_adaptive": (_int, [_D, _I, _dbl, _dbl, _dbl, _dbl, _dbl, _D, _D, _int, _I, _I]),
     "orc_set_threads": (None, [_int]),
     "orc_get_threads": (_int, []),
 }
@@ -369,6 +371,29 @@ def wilson_flow(W, dims, eps, n_steps, meas_every):
     lib().orc_wilson_flow(_dp(W.view(np.float64)), _dims(dims), float(eps), int(n_steps), int(meas_every),
                           _dp(E), _dp(Q))
     return E, Q
+
+
+def flow_trial_step(W, dims, h) -> float:
+    """One adaptive-flow trial step of size h (kept); returns the error d."""
+    return float(lib().orc_flow_trial_step(_dp(W.view(np.float64)), _dims(dims), float(h)))
+
+
+def adaptive_measurements(t_end, dt_meas) -> int:
+    """Measurement times k dt_meas <= t_end, plus t_end if it is not one."""
+    k = int(np.floor(t_end / dt_meas + 1e-9))
+    return k + 1 + (1 if t_end - k * dt_meas > 1e-12 * dt_meas else 0)
+
+
+def wilson_flow_adaptive(W, dims, t_end, tol, eps_max, eps0, dt_meas):
+    """Adaptive-step flow to t_end; returns (E, Q, steps, rejects)."""
+    m = adaptive_measurements(t_end, dt_meas)
+    E = np.zeros(m)
+    Q = np.zeros(m)
+    steps, rejects = ctypes.c_int(0), ctypes.c_int(0)
+    got = lib().orc_wilson_flow_adaptive(_dp(W.view(np.float64)), _dims(dims), float(t_end), float(tol),
+                                         float(eps_max), float(eps0), float(dt_meas), _dp(E), _dp(Q), m,
+                                         ctypes.byref(steps), ctypes.byref(rejects))
+    return E[:got], Q[:got], steps.value, rejects.value
 
 
 # ---------------------------------------------------------------- loops

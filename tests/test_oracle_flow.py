@@ -77,3 +77,84 @@ def test_flow_keeps_constant_flux_fixed(orc):
         orc.flow_step(W, dims, 0.05)
     E1, Q1 = orc.clover_EQ(W, dims)
     assert abs(E1 - E0) < 1e-12 and abs(Q1 - Q0) < 1e-11
+
+
+# ---------------------------------------------------------------- adaptive step
+# Sec. IV.B, Table II: adaptive step (embedded second-order estimate from the
+# RK3 stages), tolerance 0.01, maximal step 0.2.
+
+
+def test_adaptive_error_estimate_is_third_order(orc):
+    """d(h) = |W3 - exp(2 Z1 - Z0) W0| is the local error of a second-order
+    method: d(h) / d(h/2) -> 8.  A first-order combination (e.g. exp(Z1) W0
+    or exp(Z0) W0) gives 4, a wrong stage weight in W3 spoils the ratio."""
+    dims = [4, 4, 4, 4]
+    U = orc.init_links(dims, 1, seed=3)
+    ds = []
+    for h in (0.04, 0.02, 0.01):
+        W = U.copy()
+        ds.append(orc.flow_trial_step(W, dims, h))
+    r1, r2 = ds[0] / ds[1], ds[1] / ds[2]
+    assert 7.5 < r1 < 8.5 and 7.5 < r2 < 8.5, (ds, r1, r2)
+    # the trial step itself is the fixed RK3 step
+    W, W2 = U.copy(), U.copy()
+    orc.flow_trial_step(W, dims, 0.02)
+    orc.flow_step(W2, dims, 0.02)
+    assert np.array_equal(W, W2)
+
+
+def test_adaptive_with_loose_tolerance_is_the_fixed_step_flow(orc):
+    """tol so large that every trial is kept and the step pinned at eps_max:
+    the same arithmetic as the fixed-step flow (binary-exact step 1/16)."""
+    dims = [4, 4, 2, 4]
+    U = orc.init_links(dims, 1, seed=4)
+    W = U.copy()
+    E, Q, steps, rejects = orc.wilson_flow_adaptive(W, dims, 1.0, 1e9, 0.0625, 0.0625, 0.25)
+    Wf = U.copy()
+    Ef, Qf = orc.wilson_flow(Wf, dims, 0.0625, 16, 4)
+    assert (steps, rejects) == (16, 0)
+    assert np.array_equal(E, Ef) and np.array_equal(Q, Qf) and np.array_equal(W, Wf)
+
+
+def _thermal(orc, dims, beta, seed, n):
+    U = orc.init_links(dims, 1, seed=seed)
+    orc.update_chain(U, dims, beta, seed, 0, 0, n, 1, 4)
+    return U
+
+
+def test_adaptive_matches_fixed_step_flow_within_paper_deviation(orc):
+    """Sec. IV.B: with tolerance 0.01 and maximal step 0.2 the adaptive flow's
+    E(t) deviated from the fixed-step (0.01) flow by at most about 0.02 % up to
+    5 t0 and Q agreed per configuration.  Here: a thermalised 4^3 x 8 field at
+    the beta of the 12^3 x 24 ensemble (t0 ~ 0.73), measurements every
+    0.18 ~ t0/4.  Smaller tolerances converge to the fixed-step flow."""
+    dims, beta = [4, 4, 4, 8], 5.626
+    U = _thermal(orc, dims, beta, 11, 60)
+    Ef, Qf = orc.wilson_flow(U.copy(), dims, 0.01, 180, 18)
+    devs = []
+    for tol in (0.01, 1e-3, 1e-4):
+        W = U.copy()
+        E, Q, steps, rejects = orc.wilson_flow_adaptive(W, dims, 1.8, tol, 0.2, 0.01, 0.18)
+        assert len(E) == 11
+        devs.append(np.max(np.abs(E - Ef) / Ef))
+        assert np.max(np.abs(Q - Qf)) < 2e-3
+        assert steps >= 1.8 / 0.2
+    assert devs[0] < 2e-4, devs
+    assert devs[1] < devs[0] / 3 and devs[2] < devs[1] / 3, devs
+
+
+def test_adaptive_controller_rejects_and_lands_on_measurement_times(orc):
+    """An oversized first trial is rejected and the field restored; the run
+    still measures at every k dt_meas <= t_end and at t_end, and agrees with a
+    run whose first trial is small."""
+    dims = [4, 4, 4, 8]
+    U = _thermal(orc, dims, 5.626, 12, 30)
+    assert orc.adaptive_measurements(1.0, 0.25) == 5
+    assert orc.adaptive_measurements(1.1, 0.25) == 6
+    assert orc.adaptive_measurements(0.0, 0.25) == 1
+    Wa, Wb = U.copy(), U.copy()
+    Ea, Qa, sa, ra = orc.wilson_flow_adaptive(Wa, dims, 1.1, 1e-4, 0.2, 0.2, 0.25)
+    Eb, Qb, sb, rb = orc.wilson_flow_adaptive(Wb, dims, 1.1, 1e-4, 0.2, 0.001, 0.25)
+    assert ra >= 1 and len(Ea) == len(Eb) == 6
+    assert Ea[0] == Eb[0]
+    assert np.max(np.abs(Ea - Eb) / Eb) < 1e-5
