@@ -391,6 +391,30 @@ def multiscale_leg(api, beta_c=5.7, beta_f=6.0, n_sweeps=50, prec="f32c12"):
             "E_t1": float(E[-1]), "Q_t1": float(Q[-1])}
 
 
+def flow_leg(api, dims=(24, 24, 24, 48), beta=5.96, t0=2.79, prec="f32c12"):
+    """Wilson flow as in Sec. IV.B / Table II on the 24^3 x 48, beta = 5.96
+    ensemble (nominal t0 = 2.79): adaptive step (tolerance 0.01, maximal step
+    0.2, measurements every t0/4) to 14 t0, against the fixed step 0.01 to
+    5 t0 on the same configuration."""
+    import numpy as np
+
+    lat = api.Lattice(list(dims), prec, seed=8642)
+    api.mgq_init_links(lat, 1)
+    api.mgq_update_sweeps(lat, beta, 0, 300, 1, 4)
+    ref = api.copy_lattice(lat)
+    n_fixed = int(round(5 * t0 / 0.01))
+    (Ef, Qf), t_fix = _timed(lambda: api.mgq_wilson_flow(ref, 0.01, n_fixed, n_fixed // 5))
+    (E, Q, steps, rejects), t_ad = _timed(lambda: api.mgq_wilson_flow_adaptive(lat, 14 * t0, 0.01, 0.2, 0.01, t0 / 4))
+    Ea, Qa = E[0:21:4], Q[0:21:4]  # t = k t0, k = 0..5
+    return {"workload": f"{'x'.join(map(str, dims))} beta={beta} (300 x (HB + 4 OR) from a hot start), {prec}; "
+                        f"adaptive tol 0.01, max step 0.2, E/Q every t0/4 to 14 t0 vs fixed 0.01 to 5 t0",
+            "adaptive_ms": 1e3 * t_ad, "adaptive_steps": steps, "adaptive_rejects": rejects,
+            "fixed_ms": 1e3 * t_fix, "fixed_steps": n_fixed, "ms_per_fixed_step": 1e3 * t_fix / n_fixed,
+            "max_rel_dev_E_to_5t0": float(np.max(np.abs(Ea - Ef) / Ef)),
+            "max_abs_dev_Q_to_5t0": float(np.max(np.abs(Qa - Qf))), "Q_14t0": float(Q[-1]),
+            "t2E_at_t0": float(t0 * t0 * Ea[1])}
+
+
 def large_leg(api, beta=6.2):
     """48^4 at beta = 6.2, FP32 12-real and FP64 side by side: sweeps, HMC, flow to t = 3."""
     out = {}
@@ -552,7 +576,8 @@ def run_mgq(args, dims, world, rank, local):
         out["speedup_vs_fp64"] = (value / world) / out["fp64_plain_link_updates_per_s"]
         del lat, host_links
         torch.cuda.empty_cache()
-        legs = [("batched", batched_leg), ("hmc_24", hmc_leg), ("multiscale_16", multiscale_leg)]
+        legs = [("batched", batched_leg), ("hmc_24", hmc_leg), ("multiscale_16", multiscale_leg),
+                ("flow_24x48", flow_leg)]
         if args.large:
             legs.append(("large_48", large_leg))
         for name, fn in legs:

@@ -227,6 +227,36 @@ mgq_status mgq_topo_charge(const mgq_lattice* lat, double* E_out, double* Q_out,
 mgq_status mgq_wilson_flow(mgq_lattice* lat, double eps, int n_steps, int meas_every, double* E_out,
                            double* Q_out, void* stream);
 
+/* Adaptive-step Wilson flow (Sec. IV.B, Table II: tolerance 0.01, maximal
+ * step 0.2, measurements every t0/4).  Each trial step of size h runs the
+ * three stages above and the embedded second-order solution
+ * W2 = exp(2 Z1 - Z0) W0; d = max over links of |W3 - W2|_F / 3.  The step is
+ * kept iff d <= tol; the next trial size is h min(2, 0.95 (tol/d)^(1/3)),
+ * capped by eps_max and by the next measurement time k dt_meas (a step cut
+ * short there keeps the previous size).  eps0 is the first trial size.  The
+ * links are replaced by the field flowed to t_end.  E and Q are measured at
+ * t = k dt_meas <= t_end and at t_end: E_out, Q_out hold
+ * mgq_flow_adaptive_measurements(t_end, dt_meas) doubles (host or device, NULL
+ * to skip); n_meas, n_steps, n_rejects (host, NULL to skip) receive the
+ * measurements made, the accepted steps and the rejected trials.  The step
+ * control runs on the device; the call synchronises `stream` once per 16
+ * trials and therefore cannot be captured into a CUDA graph.  scratch: device,
+ * 256-byte aligned, >= mgq_flow_adaptive_scratch_bytes.  Uses the workspace's
+ * link copy and algebra buffer.  Errors: MGQ_EINVAL (bad arguments, more than
+ * 240 measurements, step size underflow when tol is below the precision's
+ * rounding floor, more than 2^20 trials), MGQ_ENOMEM. */
+mgq_status mgq_wilson_flow_adaptive(mgq_lattice* lat, double t_end, double tol, double eps_max, double eps0,
+                                    double dt_meas, double* E_out, double* Q_out, int* n_meas, int* n_steps,
+                                    int* n_rejects, void* scratch, uint64_t scratch_bytes, void* stream);
+
+/* Bytes of the scratch of mgq_wilson_flow_adaptive (one algebra field); 0 on
+ * invalid extents or precision. */
+uint64_t mgq_flow_adaptive_scratch_bytes(const mgq_lattice* lat);
+
+/* Number of measurements of mgq_wilson_flow_adaptive: the times k dt_meas <=
+ * t_end plus t_end when it is not one of them; -1 on invalid arguments. */
+int mgq_flow_adaptive_measurements(double t_end, double dt_meas);
+
 /* ---- adjoint Wilson flow (reverse mode through the RK3 step above) ------------
  * Cotangents are algebra fields in the mom layout and precision; a cotangent
  * L at a field W pairs with the variation W_l -> exp(e_l) W_l as

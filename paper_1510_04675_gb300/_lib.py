@@ -64,6 +64,9 @@ SIGNATURES = {
     "mgq_wilson_loop": (_st, [_P, _i, _i, _vp, _vp]),
     "mgq_partial_loops": (_st, [_P, _vp, _vp]),
     "mgq_wilson_flow": (_st, [_P, _d, _i, _i, _vp, _vp, _vp]),
+    "mgq_wilson_flow_adaptive": (_st, [_P, _d, _d, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _u64, _vp]),
+    "mgq_flow_adaptive_scratch_bytes": (ctypes.c_uint64, [_P]),
+    "mgq_flow_adaptive_measurements": (ctypes.c_int, [_d, _d]),
     "mgq_hmc_force": (_st, [_P, _d, _vp, _vp]),
     "mgq_link_exp_update": (_st, [_P, _vp, _d, _vp]),
     "mgq_flow_adjoint_scratch_bytes": (ctypes.c_uint64, [_P]),

@@ -188,6 +188,25 @@ def mgq_wilson_flow(lat: Lattice, eps: float, n_steps: int, meas_every: int, str
     return E, Q
 
 
+def mgq_wilson_flow_adaptive(lat: Lattice, t_end: float, tol: float = 0.01, eps_max: float = 0.2,
+                             eps0: float = 0.01, dt_meas: float | None = None, stream=None):
+    """Adaptive-step flow to t_end; returns (E, Q, steps, rejects), E and Q at
+    t = k dt_meas <= t_end and at t_end (dt_meas defaults to t_end)."""
+    dt = float(t_end if dt_meas is None else dt_meas)
+    L = _lib.load()
+    m = int(L.mgq_flow_adaptive_measurements(float(t_end), dt))
+    if m < 0:
+        raise ValueError("mgq_wilson_flow_adaptive: need t_end >= 0 and dt_meas > 0")
+    n = int(L.mgq_flow_adaptive_scratch_bytes(lat.ref))
+    scratch = torch.empty(n, dtype=torch.uint8, device=lat.device)
+    E, Q = np.zeros(m), np.zeros(m)
+    nm, ns, nr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    call("mgq_wilson_flow_adaptive", lat.ref, float(t_end), float(tol), float(eps_max), float(eps0), dt,
+         ctypes.c_void_p(E.ctypes.data), ctypes.c_void_p(Q.ctypes.data), ctypes.byref(nm), ctypes.byref(ns),
+         ctypes.byref(nr), _ptr(scratch), n, _stream_handle(stream))
+    return E[:nm.value], Q[:nm.value], int(ns.value), int(nr.value)
+
+
 def mgq_hmc_force(lat: Lattice, beta: float, force_out: torch.Tensor, stream=None) -> None:
     call("mgq_hmc_force", lat.ref, float(beta), _ptr(force_out), _stream_handle(stream))
 

@@ -12,7 +12,9 @@ mgq_status exp_update(const mgq_lattice* lat, void* B, double s, cudaStream_t st
 // q(x) = -1/(32 pi^2) eps Tr(G G) = 1/(8 pi^2) (g01.g23 - g02.g13 + g03.g12),
 // using Tr(X_a X_b) = -delta_ab / 2.
 template <class T, int NP>
-__global__ void __launch_bounds__(128) k_clover(Links<T, NP> U, Geom g, double* __restrict__ partials) {
+__global__ void __launch_bounds__(128) k_clover(Links<T, NP> U, Geom g, double* __restrict__ partials,
+                                               const int* __restrict__ gate) {
+    if (gate && !__ldg(gate)) return;  // grid-uniform: the whole launch skips
     double e = 0.0, q = 0.0;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.V; idx += gridDim.x * blockDim.x) {
         const int par = idx >= g.Vh, h = idx - par * g.Vh;
@@ -42,12 +44,18 @@ __global__ void __launch_bounds__(128) k_clover(Links<T, NP> U, Geom g, double* 
     }
 }
 
-mgq_status clover_into(const mgq_lattice* lat, double* partials, double* dev_out, cudaStream_t st) {
+int clover_partials(const mgq_lattice* lat, double* partials, const int* gate, cudaStream_t st) {
     const Geom g = make_geom(lat->dims);
     const int nb = reduction_blocks(g.V, 128) < 2048 ? reduction_blocks(g.V, 128) : 2048;
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
-        k_clover<T, NP><<<nb, 128, 0, st>>>(links_of<T, NP>(lat), g, partials);
+        k_clover<T, NP><<<nb, 128, 0, st>>>(links_of<T, NP>(lat), g, partials, gate);
     });
+    return nb;
+}
+
+mgq_status clover_into(const mgq_lattice* lat, double* partials, double* dev_out, cudaStream_t st) {
+    const Geom g = make_geom(lat->dims);
+    const int nb = clover_partials(lat, partials, nullptr, st);
     launch_final_sum(partials, nb, 1.0 / (double)g.V, dev_out, st);
     launch_final_sum(partials + nb, nb, 1.0, dev_out + 1, st);
     return cuda_check("clover");

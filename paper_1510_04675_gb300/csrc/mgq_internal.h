@@ -60,6 +60,9 @@ mgq_status heatbath_subsweep(mgq_lattice* lat, double beta, uint64_t sweep, int 
 mgq_status overrelax_subsweep(mgq_lattice* lat, int mu, int par, cudaStream_t st);
 // E (site average) and Q of the clover field strength into dev_out[0], dev_out[1]
 mgq_status clover_into(const mgq_lattice* lat, double* partials, double* dev_out, cudaStream_t st);
+// Per-block E and Q partial sums (E at partials[0..nb), Q at partials[nb..2nb));
+// skipped when gate != nullptr and *gate == 0.  Returns nb.
+int clover_partials(const mgq_lattice* lat, double* partials, const int* gate, cudaStream_t st);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 

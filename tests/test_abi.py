@@ -100,3 +100,13 @@ def test_block_size_settings(mgqlib):
     for bad in [(0, 2, 48), (0, 2, 256), (2, 0, 64), (1, 5, 64)]:
         assert mgqlib.mgq_set_block_size(*bad) == 1
     assert mgqlib.mgq_get_block_size(7, 0) == 0
+
+
+def test_adaptive_flow_host_helpers(mgqlib):
+    from paper_1510_04675_gb300 import _lib
+
+    f = _lib.load().mgq_flow_adaptive_measurements
+    assert [f(1.0, 0.25), f(1.1, 0.25), f(0.0, 0.25), f(3.65, 0.1825)] == [5, 6, 1, 21]
+    assert f(-1.0, 0.25) == -1 and f(1.0, 0.0) == -1 and f(float("nan"), 0.25) == -1
+    c = _lat((8, 8, 8, 8), 2)
+    assert _lib.load().mgq_flow_adaptive_scratch_bytes(ctypes.byref(c)) == 4 * 2 * 8 * 8**4 // 2 * 4
