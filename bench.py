@@ -38,6 +38,15 @@ METRIC = "link updates/s + force GB/s, 32^4 SU(3), vs plain FP64 GPU; % HBM roof
 UNIT = "link updates/s"
 LINK_BYTES = {"f64": 144, "f32": 72, "f32c12": 48}
 REAL_BYTES = {"f64": 8, "f32": 4, "f32c12": 4}
+# FP32 ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz
+# (a packed FFMA2 issues at half rate, so it does not raise this).  FP64 on this part is far lower.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Algorithmic real flops per link (complex multiply 6, complex add 2, 3x3 complex product 198):
+# staple = 12 products + 5 matrix sums = 2466; the force adds U.A (198) and the traceless
+# antihermitian projection and scaled accumulate (36); the overrelaxation adds U.A (198), three
+# SU(2) subgroup steps (about 200 each) and the reunitarisation (about 140); the heat bath adds
+# the Creutz sampler (about 60 per subgroup) to that.
+FLOPS_PER_LINK = {"k_force": 2700, "k_overrelax": 3400, "k_heatbath": 3580}
 
 
 def parse_args():
@@ -511,6 +520,14 @@ def run_mgq(args, dims, world, rank, local):
                 "traffic": traffic_from_profiles(name, tag), "kernel": name, "ms_per_launch": ms,
                 "algorithmic_bytes_per_launch": bytes_per_launch, "peak_source": peak_src}
 
+    def alu_roof(name, links, ms):
+        if args.prec == "f64":
+            return None
+        ach = FLOPS_PER_LINK[name] * links / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None, "kernel": name, "ms_per_launch": ms,
+                "algorithmic_flops_per_link": FLOPS_PER_LINK[name], "peak_source": "derived (unit counts x clock)"}
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": 1e3 * t / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -518,6 +535,8 @@ def run_mgq(args, dims, world, rank, local):
         "config": workload_config(args, dims),
         "roofline": roof(dom, kernels[dom]),
         "roofline_heatbath": roof("k_heatbath", hb_ms),
+        "roofline_alu": {"k_overrelax": alu_roof("k_overrelax", V // 2, or_ms),
+                         "k_heatbath": alu_roof("k_heatbath", V // 2, hb_ms)},
         "gpu_launches": K * (8 + 8 * n_or + 2),
         "clocks": clocks,
     }
@@ -540,6 +559,7 @@ def run_mgq(args, dims, world, rank, local):
         out["force_gbs"] = fb / (ms * 1e-3) / 1e9
         out["force_ms"] = ms
         out["force_roofline_frac"] = out["force_gbs"] / peak
+        out["force_roofline"] = alu_roof("k_force", 4 * V, ms)
     except Exception as e:  # noqa: BLE001 - reported, not hidden
         out["force_gbs"] = None
         out["force_error"] = str(e)[:200]
