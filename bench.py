@@ -433,11 +433,31 @@ def large_leg(api, beta=6.2):
         _, t_sw = _timed(lambda: api.mgq_update_sweeps(lat, beta, 0, n_sw, 1, 1))
         _, t_h = _timed(lambda: [api.mgq_hmc_trajectory(lat, beta, 1.0, 40, t, 0) for t in range(n_traj)])
         w = api.copy_lattice(lat)
-        _, t_f = _timed(lambda: api.mgq_wilson_flow(w, 0.01, n_flow, n_flow))
+        (E, Q), t_f = _timed(lambda: api.mgq_wilson_flow(w, 0.01, n_flow, n_flow))
         V = 48**4
         out[prec] = {"sweeps": n_sw, "link_updates_per_s": 2 * 4 * V * n_sw / t_sw,
-                     "ms_per_hmc_trajectory_40_steps": 1e3 * t_h / n_traj, "ms_per_flow_step": 1e3 * t_f / n_flow}
-        del lat, w
+                     "ms_per_hmc_trajectory_40_steps": 1e3 * t_h / n_traj, "ms_per_flow_step": 1e3 * t_f / n_flow,
+                     "Q_flowed": float(Q[-1])}
+        del w
+        if prec == "f32c12":
+            # dQ(W_t)/d omega at omega = 0 through the checkpointed adjoint flow (t = 3)
+            import torch
+
+            from paper_1510_04675_gb300.autograd import flowed_observable
+
+            omega = torch.zeros_like(lat.new_alg_field(), requires_grad=True)
+
+            def fwd_bwd():
+                q = flowed_observable(omega, lat, "Q", 0.01, n_flow)
+                q.backward()
+                return q
+
+            q, t_fb = _timed(fwd_bwd)
+            out[prec]["ms_flowed_Q_forward_backward"] = 1e3 * t_fb
+            out[prec]["grad_norm"] = float(omega.grad.norm())
+            out[prec]["Q_flowed_autograd"] = float(q.detach())
+            del omega
+        del lat
     return out
 
 

@@ -170,6 +170,34 @@ def test_full_size_32x4_sampled_links(gpu, orc, prec, tol):
     assert unitarity_violation(G[:, 2]) < (1e-13 if prec == "f64" else 2e-6)
 
 
+def test_full_size_48x4_sampled_links(gpu, orc):
+    """48^4 (the large-volume lattice, 5.3 M sites, the largest benchmarked
+    extent; FP32 12-real): a heat-bath sub-sweep and then an overrelaxation
+    sweep, sampled links recomputed by the oracle from the exact GPU input.
+    The direction-0 even links of the overrelaxation sweep are updated first
+    and never again, so they depend on the sweep's input field only."""
+    dims, beta, seed = [48, 48, 48, 48], 6.2, 33
+    lat = _lat(gpu, dims, "f32c12", seed=seed)
+    gpu.mgq_init_links(lat, 1)
+    U = lat.to_numpy()
+    V = U.shape[0]
+    gpu.mgq_heatbath_subsweep(lat, beta, 7, 1, 3, 0)
+    G = lat.to_numpy()
+    rng = np.random.default_rng(1)
+    sites = rng.integers(V, size=4000)
+    hb = [int(s) for s in sites if sum(orc.coords(dims, int(s))) % 2 == 0][:150]
+    for s in hb:
+        ref, _ = orc.heatbath_one_link(U, dims, beta, seed, 0, 7, 1, s, 3)
+        assert np.max(np.abs(G[s, 3] - ref)) < 2e-5
+    del U
+    gpu.mgq_overrelax_sweep(lat)
+    H = lat.to_numpy()
+    for s in hb:  # even sites: direction 0 is the first sub-sweep
+        ref = orc.overrelax_one_link(G, dims, s, 0)
+        assert np.max(np.abs(H[s, 0] - ref)) < 2e-5
+    assert unitarity_violation(H[:, 0]) < 2e-6
+
+
 def test_plaquette_parity(gpu, orc):
     dims = [6, 4, 8, 2]
     U = orc.init_links(dims, 1, seed=3)
