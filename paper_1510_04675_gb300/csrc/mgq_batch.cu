@@ -165,6 +165,7 @@ uint64_t mgq_batch_workspace_bytes(const mgq_lattice* lats, int n_lat, int n_swe
 mgq_status mgq_update_sweeps_batched(mgq_lattice* lats, int n_lat, const double* betas, uint64_t sweep0, int n_sweeps,
                                      int n_hb, int n_or, double* plaq_out, void* batch_work, uint64_t batch_work_bytes,
                                      void* stream) {
+    Trace trace("mgq_update_sweeps_batched");
     if (!lats || n_lat < 1) return fail(MGQ_EINVAL, "mgq_update_sweeps_batched: need at least one lattice");
     if (!betas) return fail(MGQ_EINVAL, "mgq_update_sweeps_batched: betas is NULL");
     mgq_status s;

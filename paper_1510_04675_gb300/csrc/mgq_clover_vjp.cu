@@ -160,6 +160,7 @@ uint64_t mgq_clover_vjp_scratch_bytes(const mgq_lattice* lat) {
 
 mgq_status mgq_clover_vjp(const mgq_lattice* lat, int observable, double scale, void* lambda, void* scratch,
                           uint64_t scratch_bytes, void* stream) {
+    Trace trace("mgq_clover_vjp");
     mgq_status s = check_lattice(lat, false, "mgq_clover_vjp");
     if (s) return s;
     if (observable != 0 && observable != 1) return fail(MGQ_EINVAL, "mgq_clover_vjp: observable must be 0 (E) or 1 (Q)");

@@ -315,6 +315,7 @@ static int g_block[2][3] = {{128, 128, 128}, {128, 128, 128}};
 
 mgq_status heatbath_subsweep(mgq_lattice* lat, double beta, uint64_t sweep, int n_hb, int mu, int par,
                              uint8_t* dec, cudaStream_t st) {
+    Trace trace("heatbath_subsweep");
     const Geom g = make_geom(lat->dims);
     const int bs = g_block[MGQ_KERNEL_HEATBATH][lat->prec];
     const RngKey rk = make_rng(lat->seed, lat->lattice_id, sweep);
@@ -327,6 +328,7 @@ mgq_status heatbath_subsweep(mgq_lattice* lat, double beta, uint64_t sweep, int 
 }
 
 mgq_status overrelax_subsweep(mgq_lattice* lat, int mu, int par, cudaStream_t st) {
+    Trace trace("overrelax_subsweep");
     const Geom g = make_geom(lat->dims);
     const int bs = g_block[MGQ_KERNEL_OVERRELAX][lat->prec];
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
@@ -392,6 +394,7 @@ int mgq_get_block_size(int kernel, int prec) {
 }
 
 mgq_status mgq_init_links(mgq_lattice* lat, int start, void* stream) {
+    Trace trace("mgq_init_links");
     mgq_status s = check_lattice(lat, false, "mgq_init_links");
     if (s) return s;
     if (start != 0 && start != 1) return fail(MGQ_EINVAL, "mgq_init_links: start must be 0 (cold) or 1 (hot)");
@@ -444,6 +447,7 @@ mgq_status mgq_heatbath_subsweep(mgq_lattice* lat, double beta, uint64_t sweep, 
 }
 
 mgq_status mgq_heatbath_sweep(mgq_lattice* lat, double beta, uint64_t sweep, int n_hb, void* stream) {
+    Trace trace("mgq_heatbath_sweep");
     mgq_status s = check_lattice(lat, false, "mgq_heatbath_sweep");
     if (s) return s;
     if ((s = check_hb_args(beta, n_hb, "mgq_heatbath_sweep"))) return s;
@@ -454,6 +458,7 @@ mgq_status mgq_heatbath_sweep(mgq_lattice* lat, double beta, uint64_t sweep, int
 }
 
 mgq_status mgq_overrelax_sweep(mgq_lattice* lat, void* stream) {
+    Trace trace("mgq_overrelax_sweep");
     mgq_status s = check_lattice(lat, false, "mgq_overrelax_sweep");
     if (s) return s;
     for (int mu = 0; mu < 4; mu++)
@@ -464,6 +469,7 @@ mgq_status mgq_overrelax_sweep(mgq_lattice* lat, void* stream) {
 
 mgq_status mgq_update_sweeps(mgq_lattice* lat, double beta, uint64_t sweep0, int n_sweeps, int n_hb, int n_or,
                              double* plaq_out, void* stream) {
+    Trace trace("mgq_update_sweeps");
     mgq_status s = check_lattice(lat, plaq_out != nullptr, "mgq_update_sweeps");
     if (s) return s;
     if ((s = check_hb_args(beta, n_hb, "mgq_update_sweeps"))) return s;
@@ -472,6 +478,7 @@ mgq_status mgq_update_sweeps(mgq_lattice* lat, double beta, uint64_t sweep0, int
     cudaStream_t st = as_stream(stream);
     double* sc = ws_scalars(lat);
     for (int i = 0; i < n_sweeps; i++) {
+        Trace sweep_trace("compound sweep");
         for (int mu = 0; mu < 4; mu++)
             for (int par = 0; par < 2; par++)
                 if ((s = heatbath_subsweep(lat, beta, sweep0 + (uint64_t)i, n_hb, mu, par, nullptr, st))) return s;
@@ -486,6 +493,7 @@ mgq_status mgq_update_sweeps(mgq_lattice* lat, double beta, uint64_t sweep0, int
 }
 
 mgq_status mgq_plaquette(const mgq_lattice* lat, double* plaq_out, void* stream) {
+    Trace trace("mgq_plaquette");
     mgq_status s = check_lattice(lat, true, "mgq_plaquette");
     if (s) return s;
     if (!plaq_out) return fail(MGQ_EINVAL, "mgq_plaquette: plaq_out is NULL");

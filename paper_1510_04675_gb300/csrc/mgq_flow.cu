@@ -68,6 +68,7 @@ using namespace mgq;
 extern "C" {
 
 mgq_status mgq_topo_charge(const mgq_lattice* lat, double* E_out, double* Q_out, void* stream) {
+    Trace trace("mgq_topo_charge");
     mgq_status s = check_lattice(lat, true, "mgq_topo_charge");
     if (s) return s;
     cudaStream_t st = as_stream(stream);
@@ -79,6 +80,7 @@ mgq_status mgq_topo_charge(const mgq_lattice* lat, double* E_out, double* Q_out,
 
 mgq_status mgq_wilson_flow(mgq_lattice* lat, double eps, int n_steps, int meas_every, double* E_out, double* Q_out,
                            void* stream) {
+    Trace trace("mgq_wilson_flow");
     mgq_status s = check_lattice(lat, true, "mgq_wilson_flow");
     if (s) return s;
     if (!(eps > 0.0) || n_steps < 0 || meas_every < 1)

@@ -228,6 +228,7 @@ int mgq_flow_adaptive_measurements(double t_end, double dt_meas) {
 mgq_status mgq_wilson_flow_adaptive(mgq_lattice* lat, double t_end, double tol, double eps_max, double eps0,
                                     double dt_meas, double* E_out, double* Q_out, int* n_meas, int* n_steps,
                                     int* n_rejects, void* scratch, uint64_t scratch_bytes, void* stream) {
+    Trace trace("mgq_wilson_flow_adaptive");
     mgq_status s = check_lattice(lat, true, "mgq_wilson_flow_adaptive");
     if (s) return s;
     if (!(t_end >= 0.0) || !(tol > 0.0) || !(eps_max > 0.0) || !(eps0 > 0.0) || !(dt_meas > 0.0))

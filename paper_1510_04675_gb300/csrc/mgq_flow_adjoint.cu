@@ -247,6 +247,7 @@ uint64_t mgq_flow_adjoint_scratch_bytes(const mgq_lattice* lat) {
 }
 
 mgq_status mgq_flow_vjp(const mgq_lattice* lat, const void* psi, double scale, void* lambda, void* stream) {
+    Trace trace("mgq_flow_vjp");
     mgq_status s = check_lattice(lat, false, "mgq_flow_vjp");
     if (s) return s;
     if (!psi || !lambda || ((uintptr_t)psi & 15) || ((uintptr_t)lambda & 15))
@@ -256,6 +257,7 @@ mgq_status mgq_flow_vjp(const mgq_lattice* lat, const void* psi, double scale, v
 
 mgq_status mgq_wilson_flow_step_adjoint(const mgq_lattice* lat, double eps, void* lambda, void* scratch,
                                         uint64_t scratch_bytes, void* stream) {
+    Trace trace("mgq_wilson_flow_step_adjoint");
     mgq_status s = check_lattice(lat, false, "mgq_wilson_flow_step_adjoint");
     if (s) return s;
     if (!(eps > 0.0)) return fail(MGQ_EINVAL, "mgq_wilson_flow_step_adjoint: eps must be > 0");

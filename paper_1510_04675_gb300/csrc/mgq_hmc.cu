@@ -160,6 +160,7 @@ using namespace mgq;
 extern "C" {
 
 mgq_status mgq_hmc_force(const mgq_lattice* lat, double beta, void* force_out, void* stream) {
+    Trace trace("mgq_hmc_force");
     mgq_status s = check_lattice(lat, false, "mgq_hmc_force");
     if (s) return s;
     if (!(beta > 0.0)) return fail(MGQ_EINVAL, "mgq_hmc_force: beta must be > 0");
@@ -177,6 +178,7 @@ mgq_status mgq_link_exp_update(mgq_lattice* lat, const void* alg, double s, void
 
 mgq_status mgq_hmc_trajectory(mgq_lattice* lat, double beta, double tau, int n_steps, uint64_t traj, int accept_reject,
                               double* dH_out, int* accepted_out, void* stream) {
+    Trace trace("mgq_hmc_trajectory");
     mgq_status s = check_lattice(lat, true, "mgq_hmc_trajectory");
     if (s) return s;
     if (!lat->mom) return fail(MGQ_EINVAL, "mgq_hmc_trajectory: lattice has no momentum buffer");

@@ -6,11 +6,21 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "mgq.h"
 #include "mgq_device.cuh"
 
 namespace mgq {
+
+// ---- tracing: an NVTX range for the lifetime of the object (a no-op unless a
+// profiler is attached)
+struct Trace {
+    explicit Trace(const char* name) { nvtxRangePushA(name); }
+    ~Trace() { nvtxRangePop(); }
+    Trace(const Trace&) = delete;
+    Trace& operator=(const Trace&) = delete;
+};
 
 // ---- errors
 mgq_status fail(mgq_status s, const char* fmt, ...);

@@ -122,6 +122,7 @@ using namespace mgq;
 extern "C" {
 
 mgq_status mgq_wilson_loop(const mgq_lattice* lat, int m, int n, double* out, void* stream) {
+    Trace trace("mgq_wilson_loop");
     mgq_status s = check_lattice(lat, true, "mgq_wilson_loop");
     if (s) return s;
     if (m < 1 || n < 1 || m > 64 || n > 64) return fail(MGQ_EINVAL, "mgq_wilson_loop: need 1 <= m, n <= 64");
@@ -139,6 +140,7 @@ mgq_status mgq_wilson_loop(const mgq_lattice* lat, int m, int n, double* out, vo
 }
 
 mgq_status mgq_partial_loops(const mgq_lattice* lat, double* out, void* stream) {
+    Trace trace("mgq_partial_loops");
     mgq_status s = check_lattice(lat, true, "mgq_partial_loops");
     if (s) return s;
     if (!out) return fail(MGQ_EINVAL, "mgq_partial_loops: out is NULL");

@@ -154,6 +154,7 @@ using namespace mgq;
 extern "C" {
 
 mgq_status mgq_restrict(const mgq_lattice* fine, mgq_lattice* coarse, void* stream) {
+    Trace trace("mgq_restrict");
     mgq_status s = check_lattice(fine, false, "mgq_restrict");
     if (s) return s;
     if ((s = check_lattice(coarse, false, "mgq_restrict"))) return s;
@@ -171,6 +172,7 @@ mgq_status mgq_restrict(const mgq_lattice* fine, mgq_lattice* coarse, void* stre
 
 mgq_status mgq_prolongate(const mgq_lattice* coarse, mgq_lattice* fine, double c, double rel_tol, int max_iter,
                           int* iters_out, double* sd_out, void* stream) {
+    Trace trace("mgq_prolongate");
     mgq_status s = check_lattice(coarse, false, "mgq_prolongate");
     if (s) return s;
     if ((s = check_lattice(fine, true, "mgq_prolongate"))) return s;
