@@ -110,8 +110,11 @@ __device__ __forceinline__ M3<T> psi_at(const Alg<T>& P, int mu, int par, int h)
 // -TA(W_m A_m Psi_m) and, for each staple factor equal to U_m in the
 // staples of the 18 links that contain it, -TA(U_m (rest of the loop with
 // Psi W inserted)) for an undaggered factor, +TA((rest) U_m^+) for a
-// daggered one.
-template <class T, int NP>
+// daggered one.  PART 0 adds the self term, PART 1 the terms (2), (3) and
+// PART 2 the terms (4), (5) of the links of the other directions (6 each),
+// PART 3 the terms (6), (7) of the links U_rho(y -+ nu) (6); four launches
+// keep each kernel's live state in registers.
+template <class T, int NP, int PART>
 __global__ void __launch_bounds__(128) k_flow_vjp(Links<T, NP> U, Geom g, Alg<T> Psi, T scl, Alg<T> Lam) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 8 * g.Vh) return;
@@ -129,44 +132,44 @@ __global__ void __launch_bounds__(128) k_flow_vjp(Links<T, NP> U, Geom g, Alg<T>
         for (int a = 0; a < 8; a++) acc[a] += sgn * t[a];
     };
     // (1) self
-    {
+    if (PART == 0) {
         const M3<T> A = staple(U, g, x, h, rho, par);
         add(mul_nn(mul_nn(Um, A), psi_at<T, NP>(Psi, rho, par, h)), T(-1));
     }
     const int frho = pick(H.fwd, rho), brho = pick(H.bwd, rho);
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
-        if (mu == rho) continue;
+        if (PART == 0 || PART == 3 || mu == rho) continue;
         const int fmu = H.fwd[mu], bmu = H.bwd[mu];
         const int l_mm = H.lex + bmu;                // y - mu       (parity op)
         const int l_mm_pr = H.lex + bmu + frho;      // y - mu + rho (parity par)
         const int l_pr = H.lex + frho;               // y + rho      (op)
         const int l_pm = H.lex + fmu;                // y + mu       (op)
         // (2) l = U_mu(y-mu): -TA(U_rho(y) U_mu(y-mu+rho)^+ U_rho(y-mu)^+ Psi_mu(y-mu) U_mu(y-mu))
-        {
+        if (PART == 1) {
             const M3<T> a = mul_nd(mul_nd(Um, U.load(mu, par, l_mm_pr >> 1)), U.load(rho, op, l_mm >> 1));
             add(mul_nn(mul_nn(a, psi_at<T, NP>(Psi, mu, op, l_mm >> 1)), U.load(mu, op, l_mm >> 1)), T(-1));
         }
         // (3) l = U_mu(y): +TA(Psi_mu(y) U_mu(y) U_rho(y+mu) U_mu(y+rho)^+ U_rho(y)^+)
-        {
+        if (PART == 1) {
             const M3<T> a = mul_nn(mul_nn(psi_at<T, NP>(Psi, mu, par, h), U.load(mu, par, h)), U.load(rho, op, l_pm >> 1));
             add(mul_nd(mul_nd(a, U.load(mu, op, l_pr >> 1)), Um), T(1));
         }
         // (4) l = U_mu(y-mu+rho): +TA(U_mu(y-mu)^+ U_rho(y-mu) Psi_mu(y-mu+rho) U_mu(y-mu+rho) U_rho(y)^+)
-        {
+        if (PART == 2) {
             const M3<T> a = mul_dn(U.load(mu, op, l_mm >> 1), U.load(rho, op, l_mm >> 1));
             const M3<T> b = mul_nn(mul_nn(a, psi_at<T, NP>(Psi, mu, par, l_mm_pr >> 1)), U.load(mu, par, l_mm_pr >> 1));
             add(mul_nd(b, Um), T(1));
         }
         // (5) l = U_mu(y+rho): -TA(U_rho(y) Psi_mu(y+rho) U_mu(y+rho) U_rho(y+mu)^+ U_mu(y)^+)
-        {
+        if (PART == 2) {
             const M3<T> a = mul_nn(mul_nn(Um, psi_at<T, NP>(Psi, mu, op, l_pr >> 1)), U.load(mu, op, l_pr >> 1));
             add(mul_nd(mul_nd(a, U.load(rho, op, l_pm >> 1)), U.load(mu, par, h)), T(-1));
         }
     }
 #pragma unroll
     for (int nu = 0; nu < 4; nu++) {
-        if (nu == rho) continue;
+        if (PART != 3 || nu == rho) continue;
         const int fnu = H.fwd[nu], bnu = H.bwd[nu];
         const int l_mn = H.lex + bnu;               // y - nu        (op)
         const int l_mn_pr = H.lex + bnu + frho;     // y - nu + rho  (par)
@@ -196,9 +199,12 @@ static mgq_status flow_vjp(const mgq_lattice* lat, const void* links, const void
                            cudaStream_t st) {
     const Geom g = make_geom(lat->dims);
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
-        k_flow_vjp<T, NP><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(
-            links_at<T, NP>(const_cast<void*>(links), lat->dims), g, alg_at<T>(const_cast<void*>(psi), lat->dims),
-            (T)scl, alg_at<T>(lam, lat->dims));
+        const Links<T, NP> W = links_at<T, NP>(const_cast<void*>(links), lat->dims);
+        const Alg<T> P = alg_at<T>(const_cast<void*>(psi), lat->dims), L = alg_at<T>(lam, lat->dims);
+        k_flow_vjp<T, NP, 0><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(W, g, P, (T)scl, L);
+        k_flow_vjp<T, NP, 1><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(W, g, P, (T)scl, L);
+        k_flow_vjp<T, NP, 2><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(W, g, P, (T)scl, L);
+        k_flow_vjp<T, NP, 3><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(W, g, P, (T)scl, L);
     });
     return cuda_check("flow_vjp");
 }
