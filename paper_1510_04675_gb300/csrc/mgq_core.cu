@@ -224,9 +224,16 @@ __global__ void k_export(Links<T, NP> U, Geom g, double* __restrict__ canon) {
 // One thread per link of the (MU, par) subset; MU is a template parameter so
 // that every neighbour index is resolved at compile time.  Four resident
 // blocks of 128 threads per SM (at most 128 registers) measured fastest.
-template <class T, int NP, int MU>
+// FAST: the instance for one heat-bath attempt per subgroup without decision
+// recording (the benchmarked setting); the compiler removes the attempt loop
+// and the recording code.
+template <class T, int NP, int MU, bool FAST>
 __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4) k_heatbath(Links<T, NP> U, Geom g, int par, T beta, RngKey rk, int n_hb,
                                                     uint8_t* __restrict__ dec) {
+    if constexpr (FAST) {
+        n_hb = 1;
+        dec = nullptr;
+    }
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= g.Vh) return;
     int x[4];
@@ -321,7 +328,12 @@ mgq_status heatbath_subsweep(mgq_lattice* lat, double beta, uint64_t sweep, int 
     const RngKey rk = make_rng(lat->seed, lat->lattice_id, sweep);
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
         dispatch_mu(mu, [&]<int MU>() {
-            k_heatbath<T, NP, MU><<<nblk(g.Vh, bs), bs, 0, st>>>(links_of<T, NP>(lat), g, par, (T)beta, rk, n_hb, dec);
+            if (n_hb == 1 && !dec)
+                k_heatbath<T, NP, MU, true><<<nblk(g.Vh, bs), bs, 0, st>>>(links_of<T, NP>(lat), g, par, (T)beta, rk,
+                                                                           n_hb, dec);
+            else
+                k_heatbath<T, NP, MU, false><<<nblk(g.Vh, bs), bs, 0, st>>>(links_of<T, NP>(lat), g, par, (T)beta, rk,
+                                                                            n_hb, dec);
         });
     });
     return cuda_check("mgq_heatbath");
