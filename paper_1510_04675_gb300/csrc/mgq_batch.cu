@@ -50,9 +50,11 @@ __device__ __forceinline__ Geom geom_of(const LatDesc<T>& d) {
     return g;
 }
 
-template <class T, int NP, int MU>
+// NHB1: single-attempt instance (the attempt loop is removed at compile time)
+template <class T, int NP, int MU, bool NHB1>
 __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4)
     k_heatbath_batched(const __grid_constant__ Batch<T> B, int par, uint32_t idx_lo, uint32_t idx_hi, int n_hb) {
+    if constexpr (NHB1) n_hb = 1;
     const int l = find_lattice(B, blockIdx.x);
     const LatDesc<T>& d = B.d[l];
     const int h = (blockIdx.x - B.prefix[l]) * BATCH_THREADS + threadIdx.x;
@@ -200,8 +202,12 @@ mgq_status mgq_update_sweeps_batched(mgq_lattice* lats, int n_lat, const double*
                 for (int mu = 0; mu < 4; mu++)
                     for (int par = 0; par < 2; par++)
                         dispatch_mu(mu, [&]<int MU>() {
-                            k_heatbath_batched<T, NP, MU><<<nblocks, BATCH_THREADS, 0, st>>>(
-                                Bl, par, (uint32_t)(sweep & 0xffffffffu), (uint32_t)(sweep >> 32), n_hb);
+                            if (n_hb == 1)
+                                k_heatbath_batched<T, NP, MU, true><<<nblocks, BATCH_THREADS, 0, st>>>(
+                                    Bl, par, (uint32_t)(sweep & 0xffffffffu), (uint32_t)(sweep >> 32), n_hb);
+                            else
+                                k_heatbath_batched<T, NP, MU, false><<<nblocks, BATCH_THREADS, 0, st>>>(
+                                    Bl, par, (uint32_t)(sweep & 0xffffffffu), (uint32_t)(sweep >> 32), n_hb);
                         });
                 for (int k = 0; k < n_or; k++)
                     for (int mu = 0; mu < 4; mu++)
