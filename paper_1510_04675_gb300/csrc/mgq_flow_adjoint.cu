@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(128) k_flow_vjp(Links<T, NP> U, Geom g, Alg<T>
         const M3<T> A = staple(U, g, x, h, rho, par);
         add(mul_nn(mul_nn(Um, A), psi_at<T, NP>(Psi, rho, par, h)), T(-1));
     }
-    const int frho = pick(H.fwd, rho), brho = pick(H.bwd, rho);
+    const int frho = pick(H.fwd, rho);
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
         if (PART == 0 || PART == 3 || mu == rho) continue;
@@ -187,7 +187,6 @@ __global__ void __launch_bounds__(128) k_flow_vjp(Links<T, NP> U, Geom g, Alg<T>
             add(mul_nd(mul_nd(a, U.load(nu, op, l_pr_ >> 1)), Um), T(1));
         }
     }
-    (void)brho;
     T* b = Lam.at(rho, par, h);
 #pragma unroll
     for (int a = 0; a < 8; a++) b[(size_t)a * Lam.S] += scl * acc[a];
@@ -280,7 +279,7 @@ mgq_status mgq_wilson_flow_step_adjoint(const mgq_lattice* lat, double eps, void
     void* Z[3] = {p + 2 * lb, p + 2 * lb + ab, p + 2 * lb + 2 * ab};
     void* Xi[3] = {p + 2 * lb + 3 * ab, p + 2 * lb + 4 * ab, p + 2 * lb + 5 * ab};
     void* Psi = p + 2 * lb + 6 * ab;
-    const uint64_t lbytes = links_bytes(lat), abytes = alg_bytes(lat);
+    const uint64_t lbytes = links_bytes(lat);
     // forward recompute of the step from W0 = lat->links (left unchanged)
     mgq_lattice w = *lat;
     if ((s = force_accumulate(lat, Z[0], -eps, 0.0, st))) return s;  // Z0 = eps Z(W0)
@@ -307,7 +306,6 @@ mgq_status mgq_wilson_flow_step_adjoint(const mgq_lattice* lat, double eps, void
     if ((s = dexp_adjoint(lat, Z[0], Z[1], Z[2], 0.25, 0.0, 0.0, lambda, Xi[0], st))) return s;
     if ((s = combine(lat, Psi, Xi[0], Xi[1], Xi[2], 0.25, -17.0 / 36.0, 17.0 / 36.0, st))) return s;
     if ((s = flow_vjp(lat, lat->links, Psi, eps, lambda, st))) return s;
-    (void)abytes;
     return MGQ_OK;
 }
 

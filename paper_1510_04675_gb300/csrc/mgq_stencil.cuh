@@ -95,13 +95,10 @@ __device__ __forceinline__ M3<T> staple_two_row(const Links<T, NP>& U, const Geo
     return A;
 }
 
+// Full products in the oracle's order (the FP64 parity path).
 template <class T, int NP>
-__device__ __forceinline__ M3<T> staple(const Links<T, NP>& U, const Geom& g, const int x[4], int h, int mu, int par) {
-    if constexpr (sizeof(T) == 4) {
-        // FP32 (both formats): products of SU(3) factors in two-row form; the
-        // FP64 parity path below keeps full products in the oracle's order.
-        return staple_two_row(U, g, x, h, mu, par);
-    }
+__device__ __forceinline__ M3<T> staple_full(const Links<T, NP>& U, const Geom& g, const int x[4], int h, int mu,
+                                             int par) {
     M3<T> A;
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -134,6 +131,14 @@ __device__ __forceinline__ M3<T> staple(const Links<T, NP>& U, const Geom& g, co
         acc_add(A, up);
     }
     return A;
+}
+
+// FP32 (both formats): products of SU(3) factors in two-row form; FP64: full
+// products in the oracle's order.
+template <class T, int NP>
+__device__ __forceinline__ M3<T> staple(const Links<T, NP>& U, const Geom& g, const int x[4], int h, int mu, int par) {
+    if constexpr (sizeof(T) == 4) return staple_two_row(U, g, x, h, mu, par);
+    else return staple_full(U, g, x, h, mu, par);
 }
 
 // =============================================================== plaquette
