@@ -19,8 +19,7 @@ constexpr int BATCH_THREADS = 128;
 template <class T>
 struct LatDesc {
     Cx<T>* links;
-    int L[4];
-    int V, Vh, S;
+    Geom g;
     T beta;
     uint2 key;
 };
@@ -43,11 +42,8 @@ __device__ __forceinline__ int find_lattice(const Batch<T>& B, int b) {
 }
 
 template <class T>
-__device__ __forceinline__ Geom geom_of(const LatDesc<T>& d) {
-    Geom g;
-    for (int m = 0; m < 4; m++) g.L[m] = d.L[m];
-    g.V = d.V; g.Vh = d.Vh; g.S = d.S;
-    return g;
+__device__ __forceinline__ const Geom& geom_of(const LatDesc<T>& d) {
+    return d.g;
 }
 
 // NHB1: single-attempt instance (the attempt loop is removed at compile time)
@@ -58,11 +54,11 @@ __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4)
     const int l = find_lattice(B, blockIdx.x);
     const LatDesc<T>& d = B.d[l];
     const int h = (blockIdx.x - B.prefix[l]) * BATCH_THREADS + threadIdx.x;
-    if (h >= d.Vh) return;
+    if (h >= d.g.Vh) return;
     const Geom g = geom_of(d);
     Links<T, NP> U;
     U.p = d.links;
-    U.S = d.S;
+    U.S = d.g.S;
     RngKey rk;
     rk.key = d.key;
     rk.idx_lo = idx_lo;
@@ -80,11 +76,11 @@ __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4) k_overr
     const int l = find_lattice(B, blockIdx.x);
     const LatDesc<T>& d = B.d[l];
     const int h = (blockIdx.x - B.prefix[l]) * BATCH_THREADS + threadIdx.x;
-    if (h >= d.Vh) return;
+    if (h >= d.g.Vh) return;
     const Geom g = geom_of(d);
     Links<T, NP> U;
     U.p = d.links;
-    U.S = d.S;
+    U.S = d.g.S;
     int x[4];
     cb_coords(g, par, h, x);
     const M3<T> A = staple(U, g, x, h, MU, par);
@@ -95,16 +91,16 @@ __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4) k_overr
 
 // per-lattice plaquette: blocks of 256 sites, partial sums at the global block index
 template <class T, int NP>
-__global__ void __launch_bounds__(256) k_plaquette_batched(const __grid_constant__ Batch<T> B, double* __restrict__ partials) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_plaquette_batched(const __grid_constant__ Batch<T> B, double* __restrict__ partials) {
     const int l = find_lattice(B, blockIdx.x);
     const LatDesc<T>& d = B.d[l];
     const int idx = (blockIdx.x - B.prefix[l]) * 256 + threadIdx.x;
     double acc = 0.0;
-    if (idx < d.V) {
+    if (idx < d.g.V) {
         Links<T, NP> U;
         U.p = d.links;
-        U.S = d.S;
-        const int par = idx >= d.Vh, h = idx - par * d.Vh;
+        U.S = d.g.S;
+        const int par = idx >= d.g.Vh, h = idx - par * d.g.Vh;
         acc = site_plaquettes(U, geom_of(d), par, h);
     }
     acc = block_sum(acc);
@@ -119,7 +115,7 @@ __global__ void k_plaquette_batched_final(const __grid_constant__ Batch<T> B, co
     double v = 0.0;
     for (int i = B.prefix[l] + threadIdx.x; i < B.prefix[l + 1]; i += blockDim.x) v += partials[i];
     v = block_sum(v);
-    if (threadIdx.x == 0) out[l] = v / (18.0 * (double)B.d[l].V);
+    if (threadIdx.x == 0) out[l] = v / (18.0 * (double)B.d[l].g.V);
 }
 
 template <class T>
@@ -132,8 +128,7 @@ static void fill_batch(Batch<T>& B, const mgq_lattice* lats, const double* betas
         const Geom g = make_geom(L.dims);
         LatDesc<T>& d = B.d[i];
         d.links = reinterpret_cast<Cx<T>*>(L.links);
-        for (int m = 0; m < 4; m++) d.L[m] = g.L[m];
-        d.V = g.V; d.Vh = g.Vh; d.S = g.S;
+        d.g = g;
         d.beta = betas ? (T)betas[first + i] : T(1);
         const RngKey rk = make_rng(L.seed, L.lattice_id, 0);
         d.key = rk.key;

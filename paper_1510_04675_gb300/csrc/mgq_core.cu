@@ -49,6 +49,7 @@ Geom make_geom(const int32_t dims[4]) {
     g.V = dims[0] * dims[1] * dims[2] * dims[3];
     g.Vh = g.V / 2;
     g.S = (int)site_stride(dims);
+    set_divisors(g);
     return g;
 }
 
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4) k_overrelax(Links
 
 // =============================================================== plaquette
 template <class T, int NP>
-__global__ void __launch_bounds__(256) k_plaquette(Links<T, NP> U, Geom g, double* __restrict__ partials) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_plaquette(Links<T, NP> U, Geom g, double* __restrict__ partials) {
     double acc = 0.0;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.V; idx += gridDim.x * blockDim.x) {
         const int par = idx >= g.Vh, h = idx - par * g.Vh;

@@ -255,21 +255,43 @@ template <class T> __device__ __forceinline__ void reunitarize(M3<T>& u) {
 }
 
 // ----------------------------------------------------------------- geometry
-// Extents, volume, half volume and the padded per-parity site stride.
+// Extents, volume, half volume and the padded per-parity site stride, with
+// multiply-high constants for the divisions by L0, L1, L2 (set_divisors).
 struct Geom {
     int L[4];
     int V, Vh, S;
+    unsigned mg[3];
+    int sh[3];
 };
+
+// Division by an invariant integer through a multiply-high (Granlund and
+// Montgomery, PLDI 1994): for 2^(l-1) < L <= 2^l and m = ceil(2^(31+l) / L),
+// floor(n / L) = floor(n m / 2^(31+l)) for every 0 <= n < 2^31; the product's
+// high word shifted right by l - 1 gives it.  Site indices stay below 2^30.
+inline void set_divisors(Geom& g) {
+    for (int d = 0; d < 3; d++) {
+        const unsigned long long L = (unsigned long long)g.L[d];
+        int l = 0;
+        while ((1ull << l) < L) l++;
+        const unsigned long long p = 1ull << (31 + l);
+        g.mg[d] = (unsigned)(p / L + (p % L ? 1 : 0));
+        g.sh[d] = l - 1;
+    }
+}
+
+__device__ __forceinline__ int div_L(const Geom& g, int d, int n) {
+    return (int)(__umulhi((unsigned)n, g.mg[d]) >> g.sh[d]);
+}
 
 // Coordinates of checkerboard site (parity, h); h = lex/2.
 __device__ __forceinline__ void cb_coords(const Geom& g, int par, int h, int x[4]) {
-    int lex2 = 2 * h;
-    int x0e = lex2 % g.L[0];
-    int r = lex2 / g.L[0];
-    x[1] = r % g.L[1];
-    r /= g.L[1];
-    x[2] = r % g.L[2];
-    x[3] = r / g.L[2];
+    const int lex2 = 2 * h;
+    const int r0 = div_L(g, 0, lex2);
+    const int x0e = lex2 - r0 * g.L[0];
+    const int r1 = div_L(g, 1, r0);
+    x[1] = r0 - r1 * g.L[1];
+    x[3] = div_L(g, 2, r1);
+    x[2] = r1 - x[3] * g.L[2];
     x[0] = x0e + ((par ^ (x[1] + x[2] + x[3])) & 1);
 }
 

@@ -152,14 +152,36 @@ __device__ __forceinline__ double site_plaquettes(const Links<T, NP>& U, const G
     double acc = 0.0;
 #pragma unroll
     for (int mu = 0; mu < 3; mu++) {
-        const M3<T> umu = U.load(mu, par, h);
         const int hpm = (H.lex + H.fwd[mu]) >> 1;
+        if constexpr (sizeof(T) == 4) {
+            // FP32: a = U_mu(x) U_nu(x+mu) and b = U_nu(x) U_mu(x+nu) are in SU(3),
+            // so rows 0, 1 of each suffice: with s_ij = row_i(a) . conj(row_j(b)),
+            // Tr(a b^+) = s00 + s11 + conj(s00 s11 - s01 s10) (row 2 = conj(row0 x row1)
+            // and the Binet-Cauchy identity for the cross products).
+            const M3<T> umu = U.load_rows(mu, par, h);
 #pragma unroll
-        for (int nu = mu + 1; nu < 4; nu++) {
-            const int hpn = (H.lex + H.fwd[nu]) >> 1;
-            const M3<T> a = mul_nn(umu, U.load(nu, op, hpm));
-            const M3<T> b = mul_nn(U.load(nu, par, h), U.load(mu, op, hpn));
-            acc += (double)retr_nd(a, b);
+            for (int nu = mu + 1; nu < 4; nu++) {
+                const int hpn = (H.lex + H.fwd[nu]) >> 1;
+                const M3<T> a = mul_nn_2(umu, U.load(nu, op, hpm));
+                const M3<T> b = mul_nn_2(U.load_rows(nu, par, h), U.load(mu, op, hpn));
+                Cx<T> sij[2][2];
+#pragma unroll
+                for (int i = 0; i < 2; i++)
+#pragma unroll
+                    for (int j = 0; j < 2; j++)
+                        sij[i][j] = mulc(a.e[i][0], b.e[j][0]) + mulc(a.e[i][1], b.e[j][1]) + mulc(a.e[i][2], b.e[j][2]);
+                const Cx<T> d = sij[0][0] * sij[1][1] - sij[0][1] * sij[1][0];
+                acc += (double)(sij[0][0].re + sij[1][1].re + d.re);
+            }
+        } else {
+            const M3<T> umu = U.load(mu, par, h);
+#pragma unroll
+            for (int nu = mu + 1; nu < 4; nu++) {
+                const int hpn = (H.lex + H.fwd[nu]) >> 1;
+                const M3<T> a = mul_nn(umu, U.load(nu, op, hpm));
+                const M3<T> b = mul_nn(U.load(nu, par, h), U.load(mu, op, hpn));
+                acc += (double)retr_nd(a, b);
+            }
         }
     }
     return acc;
