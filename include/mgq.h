@@ -24,8 +24,10 @@
  *
  * Device link layout (owned by the caller, written by the library)
  * ----------------------------------------------------------------
- *   links[mu][parity][plane][h], mu = 0..3, parity = 0..1,
- *   h = lex/2 in 0..V/2-1, site stride S = mgq_site_stride(dims) >= V/2.
+ *   links[mu][parity][h/32][plane][h%32], mu = 0..3, parity = 0..1,
+ *   h = lex/2 in 0..V/2-1, site stride S = mgq_site_stride(dims) >= V/2 (a
+ *   multiple of 64): per (mu, parity), S/32 blocks of 32 consecutive sites,
+ *   each holding plane 0 of its 32 sites, then plane 1, and so on.
  *   Each element of a plane is one complex number of the link matrix U_mu(x)
  *   (re, im adjacent):
  *     MGQ_F64     : 9 planes (row-major 3x3) of double2   -> 144 B per link

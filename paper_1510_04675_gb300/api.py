@@ -286,7 +286,7 @@ def copy_lattice(lat: Lattice, with_mom: bool = False) -> Lattice:
 
 
 # ------------------------------------------------------------------ checkpoints
-_MAGIC = b"MGQCKPT1"
+_MAGIC = b"MGQCKPT2"  # 2: links in 32-site blocks of planes
 
 
 def save_checkpoint(lat: Lattice, path: str, beta: float, sweep: int) -> None:

@@ -346,15 +346,19 @@ __device__ __forceinline__ Cx<float> ldg_cx(const Cx<float>* p) {
     return mk(v.x, v.y);
 }
 
-// Link field in the [mu][parity][plane][site] layout; NP = 9 (full matrix)
-// or 6 (rows 0 and 1; row 2 rebuilt on load).
+// Link field: for each (mu, parity) the sites h = 0..S-1 come in blocks of 32
+// consecutive h; a block holds plane 0 of its 32 sites, then plane 1, ...,
+// i.e. links[mu][parity][h/32][plane][h%32].  NP = 9 planes (full matrix) or
+// 6 (rows 0 and 1; row 2 rebuilt on load).  A warp reading one plane of 32
+// consecutive sites reads 256 contiguous bytes, and the planes of one link sit
+// at fixed 256-byte (FP32) steps, so a link costs one address computation.
 template <class T, int NP>
 struct Links {
     Cx<T>* p;
-    int S;
+    int S;  // sites per (mu, parity), a multiple of 64
 
-    __device__ __forceinline__ const Cx<T>* base(int mu, int par, int h) const {
-        return p + (size_t)((mu * 2 + par) * NP) * (size_t)S + h;
+    __device__ __forceinline__ Cx<T>* base(int mu, int par, int h) const {
+        return p + ((size_t)((mu * 2 + par) * (S >> 5) + (h >> 5)) * NP << 5) + (h & 31);
     }
     __device__ __forceinline__ M3<T> load(int mu, int par, int h) const {
         const Cx<T>* b = base(mu, par, h);
@@ -362,7 +366,7 @@ struct Links {
 #pragma unroll
         for (int r = 0; r < NP / 3; r++)
 #pragma unroll
-            for (int c = 0; c < 3; c++) m.e[r][c] = ldg_cx(b + (size_t)(r * 3 + c) * S);
+            for (int c = 0; c < 3; c++) m.e[r][c] = ldg_cx(b + ((r * 3 + c) << 5));
         if (NP == 6) rebuild_row2(m);
         return m;
     }
@@ -373,17 +377,17 @@ struct Links {
 #pragma unroll
         for (int r = 0; r < 2; r++)
 #pragma unroll
-            for (int c = 0; c < 3; c++) m.e[r][c] = ldg_cx(b + (size_t)(r * 3 + c) * S);
+            for (int c = 0; c < 3; c++) m.e[r][c] = ldg_cx(b + ((r * 3 + c) << 5));
         return m;
     }
     // load of a link given its lexicographic site (parity from the site)
     __device__ __forceinline__ M3<T> load_lex(int mu, int lex, int par) const { return load(mu, par, lex >> 1); }
     __device__ __forceinline__ void store(int mu, int par, int h, const M3<T>& m) const {
-        Cx<T>* b = p + (size_t)((mu * 2 + par) * NP) * (size_t)S + h;
+        Cx<T>* b = base(mu, par, h);
 #pragma unroll
         for (int r = 0; r < NP / 3; r++)
 #pragma unroll
-            for (int c = 0; c < 3; c++) b[(size_t)(r * 3 + c) * S] = m.e[r][c];
+            for (int c = 0; c < 3; c++) b[(r * 3 + c) << 5] = m.e[r][c];
     }
 };
 

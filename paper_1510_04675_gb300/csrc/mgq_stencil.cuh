@@ -58,8 +58,8 @@ template <> __device__ __forceinline__ M3<float> mul_dn_2<float>(const M3<float>
 // (the left factor) is never completed.
 //   up = (a b^+) c^+            a = U_nu(x+mu), b = U_mu(x+nu), c = U_nu(x)
 //   dn = (e d)^+ f              d = U_nu(x+mu-nu), e = U_mu(x-nu), f = U_nu(x-nu)
-template <class T, int NP>
-__device__ __forceinline__ M3<T> staple_two_row(const Links<T, NP>& U, const Geom& g, const int x[4], int h, int mu,
+template <class T, class LinkField>
+__device__ __forceinline__ M3<T> staple_two_row(const LinkField& U, const Geom& g, const int x[4], int h, int mu,
                                                 int par) {
     M3<T> A;
 #pragma unroll
@@ -137,7 +137,7 @@ __device__ __forceinline__ M3<T> staple_full(const Links<T, NP>& U, const Geom& 
 // products in the oracle's order.
 template <class T, int NP>
 __device__ __forceinline__ M3<T> staple(const Links<T, NP>& U, const Geom& g, const int x[4], int h, int mu, int par) {
-    if constexpr (sizeof(T) == 4) return staple_two_row(U, g, x, h, mu, par);
+    if constexpr (sizeof(T) == 4) return staple_two_row<T>(U, g, x, h, mu, par);
     else return staple_full(U, g, x, h, mu, par);
 }
 
