@@ -24,17 +24,19 @@ __global__ void __launch_bounds__(128) k_clover(Links<T, NP> U, Geom g, double* 
         const int pl[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
 #pragma unroll 1
         for (int p = 0; p < 6; p++) clover_coeffs(U, g, x, par, h, pl[p][0], pl[p][1], G[p]);
-        double es = 0.0, d01_23 = 0.0, d02_13 = 0.0, d03_12 = 0.0;
+        // per-site sums in the link precision (FP64 arithmetic is slow on this
+        // part), accumulated over sites in FP64
+        T es = T(0), d01_23 = T(0), d02_13 = T(0), d03_12 = T(0);
 #pragma unroll
         for (int a = 0; a < 8; a++) {
 #pragma unroll
-            for (int p = 0; p < 6; p++) es += (double)G[p][a] * (double)G[p][a];
-            d01_23 += (double)G[0][a] * (double)G[5][a];
-            d02_13 += (double)G[1][a] * (double)G[4][a];
-            d03_12 += (double)G[2][a] * (double)G[3][a];
+            for (int p = 0; p < 6; p++) es += G[p][a] * G[p][a];
+            d01_23 += G[0][a] * G[5][a];
+            d02_13 += G[1][a] * G[4][a];
+            d03_12 += G[2][a] * G[3][a];
         }
-        e += 0.5 * es;
-        q += (d01_23 - d02_13 + d03_12) * (1.0 / (8.0 * 9.869604401089358));
+        e += 0.5 * (double)es;
+        q += ((double)d01_23 - (double)d02_13 + (double)d03_12) * (1.0 / (8.0 * 9.869604401089358));
     }
     e = block_sum(e);
     q = block_sum(q);

@@ -154,16 +154,18 @@ __global__ void __launch_bounds__(128) k_flow_error(Links<T, NP> U, Links<T, NP>
         Y.load(mu, par, h, y);
         const M3<T> w2 = mul_nn(exp_alg(y), U0.load(mu, par, h));
         const M3<T> w3 = U.load(mu, par, h);
-        double s2 = 0.0;
+        // in the link precision: an FP32 estimate steers the step as well as
+        // an FP64 one, and FP64 arithmetic is slow on this part
+        T s2 = T(0);
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int j = 0; j < 3; j++) {
-                const double dr = (double)w3.e[i][j].re - (double)w2.e[i][j].re;
-                const double di = (double)w3.e[i][j].im - (double)w2.e[i][j].im;
+                const T dr = w3.e[i][j].re - w2.e[i][j].re;
+                const T di = w3.e[i][j].im - w2.e[i][j].im;
                 s2 += dr * dr + di * di;
             }
-        d = sqrt(s2) / 3.0;
+        d = (double)(m_sqrt(s2) / T(3));
     }
     // Non-negative doubles order like their bit patterns, and a NaN compares
     // above every number, so a broken step is rejected.
