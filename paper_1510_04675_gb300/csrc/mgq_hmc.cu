@@ -68,13 +68,15 @@ __global__ void __launch_bounds__(256) k_mom_refresh(Alg<T> P, Geom g, RngKey rk
             const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
             for (int q = 0; q < 2; q++) {
-                // Box-Muller in FP64 for both precisions: the momenta set dH
-                const double u0 = u01<double>(w[2 * q]), u1 = u01<double>(w[2 * q + 1]);
-                const double rad = sqrt(-2.0 * log(u0));
-                double sn, cs;
-                sincospi(2.0 * u1, &sn, &cs);
-                p[4 * call + 2 * q] = (T)(rad * cs);
-                p[4 * call + 2 * q + 1] = (T)(rad * sn);
+                // Box-Muller in the momentum precision: FP64 for the parity path
+                // (the oracle's momenta), FP32 otherwise (FP64 transcendentals
+                // are slow on this part; the stored momenta are FP32 anyway)
+                const T u0 = u01<T>(w[2 * q]), u1 = u01<T>(w[2 * q + 1]);
+                const T rad = m_sqrt(T(-2) * m_log(u0));
+                T sn, cs;
+                sincospi(T(2) * u1, &sn, &cs);
+                p[4 * call + 2 * q] = rad * cs;
+                p[4 * call + 2 * q + 1] = rad * sn;
             }
         }
         P.store(mu, par, h, p);
