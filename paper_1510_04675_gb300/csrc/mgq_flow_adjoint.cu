@@ -106,90 +106,89 @@ __device__ __forceinline__ M3<T> psi_at(const Alg<T>& P, int mu, int par, int h)
     return alg_matrix(c);
 }
 
-// Lam_m += scale * DZ(W)*[Psi]_m for every link m = U_rho(y): the self term
-// -TA(W_m A_m Psi_m) and, for each staple factor equal to U_m in the
-// staples of the 18 links that contain it, -TA(U_m (rest of the loop with
-// Psi W inserted)) for an undaggered factor, +TA((rest) U_m^+) for a
-// daggered one.  PART 0 adds the self term, PART 1 the terms (2), (3) and
-// PART 2 the terms (4), (5) of the links of the other directions (6 each),
-// PART 3 the terms (6), (7) of the links U_rho(y -+ nu) (6); four launches
-// keep each kernel's live state in registers.
-template <class T, int NP, int PART>
-__global__ void __launch_bounds__(128) k_flow_vjp(Links<T, NP> U, Geom g, Alg<T> Psi, T scl, Alg<T> Lam) {
+// Lam_m += scale * DZ(W)*[Psi]_m for every link m = U_rho(y).  Pairing Psi
+// with Z gives sum_l Re Tr(Psi_l W_l A_l) up to a constant: every plaquette
+// holding l, traced from l, with Psi_l in front of l.  Seen from one
+// plaquette, a link it traverses forwards (as W) carries +Psi just before
+// it, one it traverses backwards (as W^+) carries -Psi just after it.  Its
+// cotangent at m is -TA(U_m R), R the rest of the loop after m with one
+// insertion at a time, summed; the insertion at m itself is the self term
+// -TA(W_m A_m Psi_m).
+
+// the self term
+template <class T, int NP>
+__global__ void __launch_bounds__(128) k_flow_vjp_self(Links<T, NP> U, Geom g, Alg<T> Psi, T scl, Alg<T> Lam) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 8 * g.Vh) return;
+    const int mp = idx / g.Vh, h = idx - mp * g.Vh, rho = mp >> 1, par = mp & 1;
+    int x[4];
+    cb_coords(g, par, h, x);
+    const M3<T> A = staple(U, g, x, h, rho, par);
+    T t[8];
+    ta_coeffs(mul_nn(mul_nn(U.load(rho, par, h), A), psi_at<T, NP>(Psi, rho, par, h)), t);
+    T* b = Lam.at(rho, par, h);
+#pragma unroll
+    for (int a = 0; a < 8; a++) b[(size_t)a * Lam.S] -= scl * t[a];
+}
+
+template <class T> __device__ __forceinline__ M3<T> msub(const M3<T>& a, const M3<T>& b) {
+    M3<T> r;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) r.e[i][j] = a.e[i][j] - b.e[i][j];
+    return r;
+}
+
+// The two plaquettes of plane (rho, nu) that hold m = U_rho(y), nu the K-th
+// direction other than rho.  Traced from m:
+//   up:   m X1 X2 X3,   X1 = U_nu(y+rho), X2 = U_rho(y+nu)^+, X3 = U_nu(y)^+
+//         R_up = Psi_nu(y+rho) X1 X2 X3 - X1 X2 Psi_rho(y+nu) X3 - X1 X2 X3 Psi_nu(y)
+//   down: m Y1 Y2 Y3,   Y1 = U_nu(y-nu+rho)^+, Y2 = U_rho(y-nu)^+, Y3 = U_nu(y-nu)
+//         R_dn = -Y1 Psi_nu(y-nu+rho) Y2 Y3 - Y1 Y2 Psi_rho(y-nu) Y3 + Y1 Y2 Psi_nu(y-nu) Y3
+// each summed by the product rule over the running prefix; SIDE 0 adds
+// scale * (-TA(U_m R_up)), SIDE 1 scale * (-TA(U_m R_dn)) (one plaquette per
+// launch keeps the live state in registers).
+template <class T, int NP, int K, int SIDE>
+__global__ void __launch_bounds__(128) k_flow_vjp_plane(Links<T, NP> U, Geom g, Alg<T> Psi, T scl, Alg<T> Lam) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 8 * g.Vh) return;
     const int mp = idx / g.Vh, h = idx - mp * g.Vh, rho = mp >> 1, par = mp & 1;
     const int op = par ^ 1;
+    const int nu = K < rho ? K : K + 1;
     int x[4];
     cb_coords(g, par, h, x);
     const Hops H = make_hops(g, x);
-    const M3<T> Um = U.load(rho, par, h);
-    T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    auto add = [&](const M3<T>& N, T sgn) {
-        T t[8];
-        ta_coeffs(N, t);
-#pragma unroll
-        for (int a = 0; a < 8; a++) acc[a] += sgn * t[a];
-    };
-    // (1) self
-    if (PART == 0) {
-        const M3<T> A = staple(U, g, x, h, rho, par);
-        add(mul_nn(mul_nn(Um, A), psi_at<T, NP>(Psi, rho, par, h)), T(-1));
-    }
     const int frho = pick(H.fwd, rho);
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        if (PART == 0 || PART == 3 || mu == rho) continue;
-        const int fmu = H.fwd[mu], bmu = H.bwd[mu];
-        const int l_mm = H.lex + bmu;                // y - mu       (parity op)
-        const int l_mm_pr = H.lex + bmu + frho;      // y - mu + rho (parity par)
-        const int l_pr = H.lex + frho;               // y + rho      (op)
-        const int l_pm = H.lex + fmu;                // y + mu       (op)
-        // (2) l = U_mu(y-mu): -TA(U_rho(y) U_mu(y-mu+rho)^+ U_rho(y-mu)^+ Psi_mu(y-mu) U_mu(y-mu))
-        if (PART == 1) {
-            const M3<T> a = mul_nd(mul_nd(Um, U.load(mu, par, l_mm_pr >> 1)), U.load(rho, op, l_mm >> 1));
-            add(mul_nn(mul_nn(a, psi_at<T, NP>(Psi, mu, op, l_mm >> 1)), U.load(mu, op, l_mm >> 1)), T(-1));
-        }
-        // (3) l = U_mu(y): +TA(Psi_mu(y) U_mu(y) U_rho(y+mu) U_mu(y+rho)^+ U_rho(y)^+)
-        if (PART == 1) {
-            const M3<T> a = mul_nn(mul_nn(psi_at<T, NP>(Psi, mu, par, h), U.load(mu, par, h)), U.load(rho, op, l_pm >> 1));
-            add(mul_nd(mul_nd(a, U.load(mu, op, l_pr >> 1)), Um), T(1));
-        }
-        // (4) l = U_mu(y-mu+rho): +TA(U_mu(y-mu)^+ U_rho(y-mu) Psi_mu(y-mu+rho) U_mu(y-mu+rho) U_rho(y)^+)
-        if (PART == 2) {
-            const M3<T> a = mul_dn(U.load(mu, op, l_mm >> 1), U.load(rho, op, l_mm >> 1));
-            const M3<T> b = mul_nn(mul_nn(a, psi_at<T, NP>(Psi, mu, par, l_mm_pr >> 1)), U.load(mu, par, l_mm_pr >> 1));
-            add(mul_nd(b, Um), T(1));
-        }
-        // (5) l = U_mu(y+rho): -TA(U_rho(y) Psi_mu(y+rho) U_mu(y+rho) U_rho(y+mu)^+ U_mu(y)^+)
-        if (PART == 2) {
-            const M3<T> a = mul_nn(mul_nn(Um, psi_at<T, NP>(Psi, mu, op, l_pr >> 1)), U.load(mu, op, l_pr >> 1));
-            add(mul_nd(mul_nd(a, U.load(rho, op, l_pm >> 1)), U.load(mu, par, h)), T(-1));
-        }
+    M3<T> R;
+    if constexpr (SIDE == 0) {
+        const int h_pr = (H.lex + frho) >> 1;             // y + rho  (op)
+        const int h_pn = (H.lex + pick(H.fwd, nu)) >> 1;  // y + nu   (op)
+        const M3<T> X1 = U.load(nu, op, h_pr);
+        const M3<T> X2d = U.load(rho, op, h_pn);  // X2 = X2d^+
+        const M3<T> P2 = mul_nd(X1, X2d);         // X1 X2
+        const M3<T> S2 = msub(mul_nd(mul_nn(psi_at<T, NP>(Psi, nu, op, h_pr), X1), X2d),
+                              mul_nn(P2, psi_at<T, NP>(Psi, rho, op, h_pn)));
+        const M3<T> X3d = U.load(nu, par, h);     // X3 = X3d^+
+        R = msub(mul_nd(S2, X3d), mul_nn(mul_nd(P2, X3d), psi_at<T, NP>(Psi, nu, par, h)));
+    } else {
+        const int bnu = pick(H.bwd, nu);
+        const int h_mn = (H.lex + bnu) >> 1;            // y - nu        (op)
+        const int h_mn_pr = (H.lex + bnu + frho) >> 1;  // y - nu + rho  (par)
+        const M3<T> Y1d = U.load(nu, par, h_mn_pr);  // Y1 = Y1d^+
+        const M3<T> Y2d = U.load(rho, op, h_mn);     // Y2 = Y2d^+
+        const M3<T> P2 = mul_dd(Y1d, Y2d);           // Y1 Y2
+        // -S2 = Y1 Psi_a Y2 + Y1 Y2 Psi_b;  R_dn = (Y1 Y2 Psi_c - (-S2)) Y3
+        M3<T> nS2 = mul_nd(mul_dn(Y1d, psi_at<T, NP>(Psi, nu, par, h_mn_pr)), Y2d);
+        acc_add(nS2, mul_nn(P2, psi_at<T, NP>(Psi, rho, op, h_mn)));
+        const M3<T> Q = msub(mul_nn(P2, psi_at<T, NP>(Psi, nu, op, h_mn)), nS2);
+        R = mul_nn(Q, U.load(nu, op, h_mn));
     }
-#pragma unroll
-    for (int nu = 0; nu < 4; nu++) {
-        if (PART != 3 || nu == rho) continue;
-        const int fnu = H.fwd[nu], bnu = H.bwd[nu];
-        const int l_mn = H.lex + bnu;               // y - nu        (op)
-        const int l_mn_pr = H.lex + bnu + frho;     // y - nu + rho  (par)
-        const int l_pn = H.lex + fnu;               // y + nu        (op)
-        const int l_pr_ = H.lex + frho;             // y + rho       (op)
-        // (6) l = U_rho(y-nu): +TA(U_nu(y-nu)^+ Psi_rho(y-nu) U_rho(y-nu) U_nu(y-nu+rho) U_rho(y)^+)
-        {
-            const M3<T> a = mul_dn(U.load(nu, op, l_mn >> 1), psi_at<T, NP>(Psi, rho, op, l_mn >> 1));
-            const M3<T> b = mul_nn(mul_nn(a, U.load(rho, op, l_mn >> 1)), U.load(nu, par, l_mn_pr >> 1));
-            add(mul_nd(b, Um), T(1));
-        }
-        // (7) l = U_rho(y+nu): +TA(U_nu(y) Psi_rho(y+nu) U_rho(y+nu) U_nu(y+rho)^+ U_rho(y)^+)
-        {
-            const M3<T> a = mul_nn(mul_nn(U.load(nu, par, h), psi_at<T, NP>(Psi, rho, op, l_pn >> 1)), U.load(rho, op, l_pn >> 1));
-            add(mul_nd(mul_nd(a, U.load(nu, op, l_pr_ >> 1)), Um), T(1));
-        }
-    }
+    T t[8];
+    ta_coeffs(mul_nn(U.load(rho, par, h), R), t);
     T* b = Lam.at(rho, par, h);
 #pragma unroll
-    for (int a = 0; a < 8; a++) b[(size_t)a * Lam.S] += scl * acc[a];
+    for (int a = 0; a < 8; a++) b[(size_t)a * Lam.S] -= scl * t[a];
 }
 
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
@@ -200,10 +199,14 @@ static mgq_status flow_vjp(const mgq_lattice* lat, const void* links, const void
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
         const Links<T, NP> W = links_at<T, NP>(const_cast<void*>(links), lat->dims);
         const Alg<T> P = alg_at<T>(const_cast<void*>(psi), lat->dims), L = alg_at<T>(lam, lat->dims);
-        k_flow_vjp<T, NP, 0><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(W, g, P, (T)scl, L);
-        k_flow_vjp<T, NP, 1><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(W, g, P, (T)scl, L);
-        k_flow_vjp<T, NP, 2><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(W, g, P, (T)scl, L);
-        k_flow_vjp<T, NP, 3><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(W, g, P, (T)scl, L);
+        k_flow_vjp_self<T, NP><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(W, g, P, (T)scl, L);
+        const int nb = nblk(8L * g.Vh, 128);
+        k_flow_vjp_plane<T, NP, 0, 0><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
+        k_flow_vjp_plane<T, NP, 0, 1><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
+        k_flow_vjp_plane<T, NP, 1, 0><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
+        k_flow_vjp_plane<T, NP, 1, 1><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
+        k_flow_vjp_plane<T, NP, 2, 0><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
+        k_flow_vjp_plane<T, NP, 2, 1><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
     });
     return cuda_check("flow_vjp");
 }
