@@ -147,19 +147,27 @@ template <class T> __device__ __forceinline__ M3<T> msub(const M3<T>& a, const M
 //   down: m Y1 Y2 Y3,   Y1 = U_nu(y-nu+rho)^+, Y2 = U_rho(y-nu)^+, Y3 = U_nu(y-nu)
 //         R_dn = -Y1 Psi_nu(y-nu+rho) Y2 Y3 - Y1 Y2 Psi_rho(y-nu) Y3 + Y1 Y2 Psi_nu(y-nu) Y3
 // each summed by the product rule over the running prefix; SIDE 0 adds
-// scale * (-TA(U_m R_up)), SIDE 1 scale * (-TA(U_m R_dn)) (one plaquette per
-// launch keeps the live state in registers).
-template <class T, int NP, int K, int SIDE>
-__global__ void __launch_bounds__(128) k_flow_vjp_plane(Links<T, NP> U, Geom g, Alg<T> Psi, T scl, Alg<T> Lam) {
+// scale * (-TA(U_m sum_nu R_up)), SIDE 1 scale * (-TA(U_m sum_nu R_dn)) (one
+// side per launch, directions in a rolled loop, keeps the live state in
+// registers).
+template <class T, int NP, int SIDE>
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 1 : 4) k_flow_vjp_plane(Links<T, NP> U, Geom g, Alg<T> Psi, T scl, Alg<T> Lam) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 8 * g.Vh) return;
     const int mp = idx / g.Vh, h = idx - mp * g.Vh, rho = mp >> 1, par = mp & 1;
     const int op = par ^ 1;
-    const int nu = K < rho ? K : K + 1;
     int x[4];
     cb_coords(g, par, h, x);
     const Hops H = make_hops(g, x);
     const int frho = pick(H.fwd, rho);
+    M3<T> Rs;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) Rs.e[i][j] = mk(T(0), T(0));
+#pragma unroll 1
+    for (int K = 0; K < 3; K++) {
+    const int nu = K < rho ? K : K + 1;
     M3<T> R;
     if constexpr (SIDE == 0) {
         const int h_pr = (H.lex + frho) >> 1;             // y + rho  (op)
@@ -184,8 +192,10 @@ __global__ void __launch_bounds__(128) k_flow_vjp_plane(Links<T, NP> U, Geom g, 
         const M3<T> Q = msub(mul_nn(P2, psi_at<T, NP>(Psi, nu, op, h_mn)), nS2);
         R = mul_nn(Q, U.load(nu, op, h_mn));
     }
+    acc_add(Rs, R);
+    }
     T t[8];
-    ta_coeffs(mul_nn(U.load(rho, par, h), R), t);
+    ta_coeffs(mul_nn(U.load(rho, par, h), Rs), t);
     T* b = Lam.at(rho, par, h);
 #pragma unroll
     for (int a = 0; a < 8; a++) b[(size_t)a * Lam.S] -= scl * t[a];
@@ -201,12 +211,8 @@ static mgq_status flow_vjp(const mgq_lattice* lat, const void* links, const void
         const Alg<T> P = alg_at<T>(const_cast<void*>(psi), lat->dims), L = alg_at<T>(lam, lat->dims);
         k_flow_vjp_self<T, NP><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(W, g, P, (T)scl, L);
         const int nb = nblk(8L * g.Vh, 128);
-        k_flow_vjp_plane<T, NP, 0, 0><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
-        k_flow_vjp_plane<T, NP, 0, 1><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
-        k_flow_vjp_plane<T, NP, 1, 0><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
-        k_flow_vjp_plane<T, NP, 1, 1><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
-        k_flow_vjp_plane<T, NP, 2, 0><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
-        k_flow_vjp_plane<T, NP, 2, 1><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
+        k_flow_vjp_plane<T, NP, 0><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
+        k_flow_vjp_plane<T, NP, 1><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
     });
     return cuda_check("flow_vjp");
 }
