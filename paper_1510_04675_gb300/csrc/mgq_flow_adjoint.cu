@@ -44,8 +44,9 @@ template <class T> __device__ __forceinline__ M3<T> commutator(const M3<T>& a, c
     return ab;
 }
 
-// Per link: X = c0 Z0 + c1 Z1 + c2 Z2; Xi = J(X)* Lam (series, 12 terms:
-// |X| is O(eps)); Lam <- e^{-X} Lam e^{X}.
+// Per link: X = c0 Z0 + c1 Z1 + c2 Z2; Xi = J(X)* Lam (series: |X| is O(eps),
+// so 12 terms reach FP64 rounding and 8 terms FP32 rounding for |X| <= 0.5);
+// Lam <- e^{-X} Lam e^{X}.
 template <class T>
 __global__ void __launch_bounds__(128) k_dexp_adjoint(Geom g, Alg<T> Z0, Alg<T> Z1, Alg<T> Z2, T c0, T c1, T c2,
                                                       Alg<T> Lam, Alg<T> Xi) {
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(128) k_dexp_adjoint(Geom g, Alg<T> Z0, Alg<T> 
     const M3<T> L = alg_matrix(l);
     M3<T> term = L, sum = L;
 #pragma unroll 1
-    for (int n = 1; n <= 12; n++) {
+    for (int n = 1; n <= (sizeof(T) == 4 ? 8 : 12); n++) {
         term = commutator(X, term);
         const T f = T(-1) / T(n + 1);
 #pragma unroll
