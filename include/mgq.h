@@ -34,7 +34,7 @@
  *     MGQ_F32     : 9 planes of float2                     ->  72 B per link
  *     MGQ_F32_C12 : 6 planes (rows 0 and 1) of float2; row 2 is rebuilt as
  *                   conj(row0 x row1) on every load        ->  48 B per link
- *   Momenta / Lie-algebra fields: mom[mu][parity][a][h], a = 0..7, the
+ *   Momenta / Lie-algebra fields: mom[mu][parity][h/32][a][h%32], a = 0..7, the
  *   coefficients p_a of P = sum_a p_a X_a, X_a = i lambda_a / 2 (Gell-Mann),
  *   as double (MGQ_F64) or float (MGQ_F32, MGQ_F32_C12).
  *

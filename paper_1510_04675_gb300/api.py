@@ -103,19 +103,43 @@ class Lattice:
         return alg_to_numpy(self, self.mom)
 
 
-def alg_to_numpy(lat: Lattice, buf: torch.Tensor) -> np.ndarray:
-    """A buffer in the momentum layout, as float64 (V, 4, 8) in lexicographic site order."""
+def _alg_blocks(lat: Lattice, buf: torch.Tensor) -> torch.Tensor:
+    """A view of an algebra buffer as [mu][parity][h/32][a][h%32] (the device layout)."""
     S = lat.site_stride
-    a = buf.view(lat.real_dtype()).reshape(4, 2, 8, S)[..., : lat.volume // 2].double().cpu().numpy()
+    return buf.view(lat.real_dtype()).reshape(4, 2, S // 32, 8, 32)
+
+
+def _site_index(lat: Lattice):
+    """Parity and half index h of every lexicographic site."""
     L = lat.dims
     idx = np.arange(lat.volume)
     x = [(idx // int(np.prod(L[:m]))) % L[m] for m in range(4)]
-    par = (x[0] + x[1] + x[2] + x[3]) % 2
-    h = idx // 2
+    return (x[0] + x[1] + x[2] + x[3]) % 2, idx // 2
+
+
+def alg_to_numpy(lat: Lattice, buf: torch.Tensor) -> np.ndarray:
+    """A buffer in the momentum layout, as float64 (V, 4, 8) in lexicographic site order."""
+    a = _alg_blocks(lat, buf).double().cpu().numpy()
+    par, h = _site_index(lat)
     out = np.empty((lat.volume, 4, 8))
     for mu in range(4):
-        out[:, mu, :] = a[mu, par, :, h]
+        out[:, mu, :] = a[mu, par, h // 32, :, h % 32]
     return out
+
+
+def alg_from_numpy(lat: Lattice, P: np.ndarray) -> torch.Tensor:
+    """A device buffer in the momentum layout from float64 (V, 4, 8) in lexicographic site order."""
+    a = np.zeros((4, 2, lat.site_stride // 32, 8, 32))
+    par, h = _site_index(lat)
+    for mu in range(4):
+        a[mu, par, h // 32, :, h % 32] = P[:, mu, :]
+    return torch.from_numpy(a.reshape(-1)).to(device=lat.device, dtype=lat.real_dtype())
+
+
+def zero_alg_padding(lat: Lattice, buf: torch.Tensor) -> None:
+    """Zero the entries of the padding sites h >= V/2 (which carry no links)."""
+    h = torch.arange(lat.volume // 2, lat.site_stride, device=buf.device)
+    _alg_blocks(lat, buf)[:, :, h // 32, :, h % 32] = 0
 
 
 # ------------------------------------------------------------------ entry points

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(128) k_clover_vjp(Links<T, NP> U, Geom g, Plan
     }
     T* out = Lam.at(rho, par, h);
 #pragma unroll
-    for (int q = 0; q < 8; q++) out[(size_t)q * Lam.S] += scl * acc[q];
+    for (int q = 0; q < 8; q++) out[q * Alg<T>::kStep] += scl * acc[q];
 }
 
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }

@@ -391,21 +391,26 @@ struct Links {
     }
 };
 
-// Lie-algebra field (8 reals per link) in the [mu][parity][a][site] layout.
+// Lie-algebra field (8 reals per link) in the link field's block layout:
+// alg[mu][parity][h/32][a][h%32].
 template <class T>
 struct Alg {
     T* p;
-    int S;
-    __device__ __forceinline__ T* at(int mu, int par, int h) const { return p + (size_t)((mu * 2 + par) * 8) * (size_t)S + h; }
+    int S;  // sites per (mu, parity), a multiple of 64
+    static constexpr int kStep = 32;  // distance between coefficients a and a+1 of one link
+
+    __device__ __forceinline__ T* at(int mu, int par, int h) const {
+        return p + ((size_t)((mu * 2 + par) * (S >> 5) + (h >> 5)) * 8 << 5) + (h & 31);
+    }
     __device__ __forceinline__ void load(int mu, int par, int h, T a[8]) const {
         const T* b = at(mu, par, h);
 #pragma unroll
-        for (int k = 0; k < 8; k++) a[k] = b[(size_t)k * S];
+        for (int k = 0; k < 8; k++) a[k] = b[k * kStep];
     }
     __device__ __forceinline__ void store(int mu, int par, int h, const T a[8]) const {
         T* b = at(mu, par, h);
 #pragma unroll
-        for (int k = 0; k < 8; k++) b[(size_t)k * S] = a[k];
+        for (int k = 0; k < 8; k++) b[k * kStep] = a[k];
     }
 };
 

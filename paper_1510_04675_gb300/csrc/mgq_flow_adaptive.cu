@@ -109,14 +109,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2)
 #pragma unroll
     for (int a = 0; a < 8; a++) {
         const T z = mh * t[a];
-        b[(size_t)a * B.S] = aB == T(0) ? cB * z : aB * b[(size_t)a * B.S] + cB * z;
+        b[a * Alg<T>::kStep] = aB == T(0) ? cB * z : aB * b[a * Alg<T>::kStep] + cB * z;
     }
     if (cY != T(0)) {
         T* y = Y.at(mu, par, h);
 #pragma unroll
         for (int a = 0; a < 8; a++) {
             const T z = mh * t[a];
-            y[(size_t)a * Y.S] = aY == T(0) ? cY * z : aY * y[(size_t)a * Y.S] + cY * z;
+            y[a * Alg<T>::kStep] = aY == T(0) ? cY * z : aY * y[a * Alg<T>::kStep] + cY * z;
         }
     }
 }

@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(128) k_flow_vjp_self(Links<T, NP> U, Geom g, A
     ta_coeffs(mul_nn(mul_nn(U.load(rho, par, h), A), psi_at<T, NP>(Psi, rho, par, h)), t);
     T* b = Lam.at(rho, par, h);
 #pragma unroll
-    for (int a = 0; a < 8; a++) b[(size_t)a * Lam.S] -= scl * t[a];
+    for (int a = 0; a < 8; a++) b[a * Alg<T>::kStep] -= scl * t[a];
 }
 
 template <class T> __device__ __forceinline__ M3<T> msub(const M3<T>& a, const M3<T>& b) {
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 1 : 4) k_flow_vjp_plane(
     ta_coeffs(mul_nn(U.load(rho, par, h), Rs), t);
     T* b = Lam.at(rho, par, h);
 #pragma unroll
-    for (int a = 0; a < 8; a++) b[(size_t)a * Lam.S] -= scl * t[a];
+    for (int a = 0; a < 8; a++) b[a * Alg<T>::kStep] -= scl * t[a];
 }
 
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }

@@ -28,10 +28,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_force(Links<T, 
     T* b = B.at(mu, par, h);
     if (alpha == T(0)) {
 #pragma unroll
-        for (int a = 0; a < 8; a++) b[(size_t)a * B.S] = coef * t[a];
+        for (int a = 0; a < 8; a++) b[a * Alg<T>::kStep] = coef * t[a];
     } else {
 #pragma unroll
-        for (int a = 0; a < 8; a++) b[(size_t)a * B.S] = alpha * b[(size_t)a * B.S] + coef * t[a];
+        for (int a = 0; a < 8; a++) b[a * Alg<T>::kStep] = alpha * b[a * Alg<T>::kStep] + coef * t[a];
     }
 }
 

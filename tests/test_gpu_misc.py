@@ -37,14 +37,8 @@ def test_link_exp_update_matches_oracle(gpu, orc):
     lat = gpu.Lattice(dims, "f64", seed=8, with_mom=True)
     lat.from_numpy(U)
     # momenta through a trajectory-free route: build the algebra buffer from the oracle's numbers
-    A = lat.new_alg_field().view(4, 2, 8, lat.site_stride)
-    V = U.shape[0]
-    for s in range(V):
-        x = orc.coords(dims, s)
-        par = sum(x) % 2
-        for mu in range(4):
-            A[mu, par, :, s // 2] = torch.from_numpy(P[s, mu])
-    gpu.mgq_link_exp_update(lat, A.reshape(-1), 0.3)
+    A = gpu.alg_from_numpy(lat, P)
+    gpu.mgq_link_exp_update(lat, A, 0.3)
     orc.update_links(U, P, dims, 0.3)
     assert np.max(np.abs(lat.to_numpy() - U)) < 1e-13
 
