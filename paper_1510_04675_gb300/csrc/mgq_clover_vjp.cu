@@ -33,7 +33,7 @@ __constant__ LeafFactor c_leaves[4][4] = {
 };
 
 template <class T>
-struct Planes6 {  // c_p(x): [p][a][parity][h]
+struct Planes6 {  // c_p(x): [p][parity][a][h] (scratch of this file only)
     T* p;
     int S;
     __device__ __forceinline__ T* at(int pl, int par, int h) const { return p + (size_t)(pl * 2 + par) * 8 * S + h; }
