@@ -148,6 +148,16 @@ mgq_status mgq_heatbath_subsweep(mgq_lattice* lat, double beta, uint64_t sweep, 
  * R = (w/|w|)^2 that keeps Re Tr(U A) unchanged).  No RNG, no beta. */
 mgq_status mgq_overrelax_sweep(mgq_lattice* lat, void* stream);
 
+/* One overrelaxation sweep, as mgq_overrelax_sweep, that also returns the
+ * average plaquette of the field it leaves (as mgq_plaquette, to rounding):
+ * the two sub-sweeps of direction 3 that end the sweep measure it on the fly
+ * (Sec. IV.A; the paper's plaquette record, Sec. III), so no separate pass
+ * reads the links.  plaq_out: one double, host or device.  Needs the
+ * workspace (it uses the algebra buffer for per-block sums).  mgq_update_sweeps
+ * uses it for the last overrelaxation sweep of each compound sweep when it
+ * records plaquettes.  Errors: MGQ_EINVAL, MGQ_ENOMEM. */
+mgq_status mgq_overrelax_sweep_plaquette(mgq_lattice* lat, double* plaq_out, void* stream);
+
 /* n_sweeps compound sweeps, each 1 heat-bath sweep (RNG index sweep0 + i)
  * followed by n_or overrelaxation sweeps (Sec. IV.A uses n_or = 10; the
  * benchmarked configurations use 4).  plaq_out (optional, n_sweeps doubles,

@@ -57,6 +57,7 @@ SIGNATURES = {
     "mgq_heatbath_sweep": (_st, [_P, _d, _u64, _i, _vp]),
     "mgq_heatbath_subsweep": (_st, [_P, _d, _u64, _i, _i, _i, _u8p, _vp]),
     "mgq_overrelax_sweep": (_st, [_P, _vp]),
+    "mgq_overrelax_sweep_plaquette": (_st, [_P, _vp, _vp]),
     "mgq_update_sweeps": (_st, [_P, _d, _u64, _i, _i, _i, _vp, _vp]),
     "mgq_plaquette": (_st, [_P, _vp, _vp]),
     "mgq_plaquette_noalloc": (_st, [_P, _vp, _vp]),

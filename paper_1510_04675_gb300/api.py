@@ -169,6 +169,17 @@ def mgq_overrelax_sweep(lat: Lattice, stream=None) -> None:
     call("mgq_overrelax_sweep", lat.ref, _stream_handle(stream))
 
 
+def mgq_overrelax_sweep_plaquette(lat: Lattice, out=None, stream=None) -> Optional[float]:
+    """One overrelaxation sweep that also measures the plaquette of the result;
+    into `out` (device tensor) or returned as a float."""
+    if out is not None:
+        call("mgq_overrelax_sweep_plaquette", lat.ref, _ptr(out), _stream_handle(stream))
+        return None
+    v = ctypes.c_double()
+    call("mgq_overrelax_sweep_plaquette", lat.ref, ctypes.byref(v), _stream_handle(stream))
+    return float(v.value)
+
+
 def mgq_update_sweeps(lat: Lattice, beta: float, sweep0: int, n_sweeps: int, n_hb: int = 1, n_or: int = 4,
                       plaq_out=None, stream=None):
     """n_sweeps x (1 HB + n_or OR); returns the per-sweep plaquettes when plaq_out is True or a tensor."""

@@ -258,6 +258,33 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4) k_overrelax(Links
     U.store(MU, par, h, u);
 }
 
+// The two sub-sweeps of direction 3, which end an overrelaxation sweep, with
+// the plaquette of the field they leave folded in (per-block FP64 partials).
+// Neither sub-sweep writes directions 0-2, so each adds the plaquettes of the
+// planes of directions 0, 1, 2 at the sites of its parity.  Every plaquette of
+// a plane (3, nu) holds exactly one direction-3 link of odd parity, and the
+// six plaquettes through U_3(x) sum to Re Tr(U_3(x) A_3(x)), which
+// overrelaxation leaves unchanged: the parity-1 sub-sweep adds it, taken
+// before the update, for each of its links.
+template <class T, int NP>
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4)
+    k_overrelax_last(Links<T, NP> U, Geom g, int par, double* __restrict__ partials) {
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (h < g.Vh) {
+        int x[4];
+        cb_coords(g, par, h, x);
+        const M3<T> A = staple(U, g, x, h, 3, par);
+        M3<T> u = U.load(3, par, h);
+        if (par == 1) acc = (double)retr_nn(u, A);
+        or_link(u, A);
+        U.store(3, par, h, u);
+        acc += site_plaquettes<T, NP, 3>(U, g, par, h);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
 // =============================================================== plaquette
 template <class T, int NP>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_plaquette(Links<T, NP> U, Geom g, double* __restrict__ partials) {
@@ -350,6 +377,26 @@ mgq_status overrelax_subsweep(mgq_lattice* lat, int mu, int par, cudaStream_t st
         });
     });
     return cuda_check("mgq_overrelax");
+}
+
+// One overrelaxation sweep whose last two sub-sweeps also measure the
+// plaquette of the result into dev_out[0] (device); needs the workspace.
+mgq_status overrelax_sweep_plaquette(mgq_lattice* lat, double* dev_out, cudaStream_t st) {
+    mgq_status s;
+    for (int mu = 0; mu < 3; mu++)
+        for (int par = 0; par < 2; par++)
+            if ((s = overrelax_subsweep(lat, mu, par, st))) return s;
+    Trace trace("overrelax_last");
+    const Geom g = make_geom(lat->dims);
+    const int bs = g_block[MGQ_KERNEL_OVERRELAX][lat->prec];
+    const int nb = nblk(g.Vh, bs);
+    double* partials = reinterpret_cast<double*>(ws_alg(lat));  // free during sweeps; >= 2 nb doubles
+    dispatch_prec(lat->prec, [&]<class T, int NP>() {
+        for (int par = 0; par < 2; par++)
+            k_overrelax_last<T, NP><<<nb, bs, 0, st>>>(links_of<T, NP>(lat), g, par, partials + par * nb);
+    });
+    launch_final_sum(partials, 2 * nb, 1.0 / (18.0 * (double)g.V), dev_out, st);
+    return cuda_check("overrelax_sweep_plaquette");
 }
 
 // plaquette of `links` into dev_out[0] (device)
@@ -495,14 +542,28 @@ mgq_status mgq_update_sweeps(mgq_lattice* lat, double beta, uint64_t sweep0, int
         for (int mu = 0; mu < 4; mu++)
             for (int par = 0; par < 2; par++)
                 if ((s = heatbath_subsweep(lat, beta, sweep0 + (uint64_t)i, n_hb, mu, par, nullptr, st))) return s;
-        for (int k = 0; k < n_or; k++)
+        // with a plaquette record, the last overrelaxation sweep measures it
+        const int n_plain = (plaq_out && n_or > 0) ? n_or - 1 : n_or;
+        for (int k = 0; k < n_plain; k++)
             for (int mu = 0; mu < 4; mu++)
                 for (int par = 0; par < 2; par++)
                     if ((s = overrelax_subsweep(lat, mu, par, st))) return s;
-        if (plaq_out && (s = plaquette_into(lat, ws_partials(lat), sc + 8 + i, st))) return s;
+        if (plaq_out && n_or > 0 && (s = overrelax_sweep_plaquette(lat, sc + 8 + i, st))) return s;
+        if (plaq_out && n_or == 0 && (s = plaquette_into(lat, ws_partials(lat), sc + 8 + i, st))) return s;
     }
     if (plaq_out) return deliver(sc + 8, plaq_out, (size_t)n_sweeps, st, "mgq_update_sweeps");
     return MGQ_OK;
+}
+
+mgq_status mgq_overrelax_sweep_plaquette(mgq_lattice* lat, double* plaq_out, void* stream) {
+    Trace trace("mgq_overrelax_sweep_plaquette");
+    mgq_status s = check_lattice(lat, true, "mgq_overrelax_sweep_plaquette");
+    if (s) return s;
+    if (!plaq_out) return fail(MGQ_EINVAL, "mgq_overrelax_sweep_plaquette: plaq_out is NULL");
+    cudaStream_t st = as_stream(stream);
+    double* sc = ws_scalars(lat);
+    if ((s = overrelax_sweep_plaquette(lat, sc + 5, st))) return s;
+    return deliver(sc + 5, plaq_out, 1, st, "mgq_overrelax_sweep_plaquette");
 }
 
 mgq_status mgq_plaquette(const mgq_lattice* lat, double* plaq_out, void* stream) {

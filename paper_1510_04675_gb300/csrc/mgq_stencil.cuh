@@ -142,8 +142,9 @@ __device__ __forceinline__ M3<T> staple(const Links<T, NP>& U, const Geom& g, co
 }
 
 // =============================================================== plaquette
-// Per site: sum over mu < nu of Re Tr[U_mu(x) U_nu(x+mu) (U_nu(x) U_mu(x+nu))^+].
-template <class T, int NP>
+// Per site: sum over mu < nu < ND of Re Tr[U_mu(x) U_nu(x+mu) (U_nu(x) U_mu(x+nu))^+]
+// (ND = 4: all six planes; ND = 3: the planes of directions 0, 1, 2).
+template <class T, int NP, int ND = 4>
 __device__ __forceinline__ double site_plaquettes(const Links<T, NP>& U, const Geom& g, int par, int h) {
     int x[4];
     cb_coords(g, par, h, x);
@@ -151,7 +152,7 @@ __device__ __forceinline__ double site_plaquettes(const Links<T, NP>& U, const G
     const Hops H = make_hops(g, x);
     double acc = 0.0;
 #pragma unroll
-    for (int mu = 0; mu < 3; mu++) {
+    for (int mu = 0; mu < ND - 1; mu++) {
         const int hpm = (H.lex + H.fwd[mu]) >> 1;
         if constexpr (sizeof(T) == 4) {
             // FP32: a = U_mu(x) U_nu(x+mu) and b = U_nu(x) U_mu(x+nu) are in SU(3),
@@ -160,7 +161,7 @@ __device__ __forceinline__ double site_plaquettes(const Links<T, NP>& U, const G
             // and the Binet-Cauchy identity for the cross products).
             const M3<T> umu = U.load_rows(mu, par, h);
 #pragma unroll
-            for (int nu = mu + 1; nu < 4; nu++) {
+            for (int nu = mu + 1; nu < ND; nu++) {
                 const int hpn = (H.lex + H.fwd[nu]) >> 1;
                 const M3<T> a = mul_nn_2(umu, U.load(nu, op, hpm));
                 const M3<T> b = mul_nn_2(U.load_rows(nu, par, h), U.load(mu, op, hpn));
@@ -176,7 +177,7 @@ __device__ __forceinline__ double site_plaquettes(const Links<T, NP>& U, const G
         } else {
             const M3<T> umu = U.load(mu, par, h);
 #pragma unroll
-            for (int nu = mu + 1; nu < 4; nu++) {
+            for (int nu = mu + 1; nu < ND; nu++) {
                 const int hpn = (H.lex + H.fwd[nu]) >> 1;
                 const M3<T> a = mul_nn(umu, U.load(nu, op, hpm));
                 const M3<T> b = mul_nn(U.load(nu, par, h), U.load(mu, op, hpn));

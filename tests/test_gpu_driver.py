@@ -37,4 +37,6 @@ def test_workflow_records(gpu, tmp_path):
     last = [r for r in recs if r["kind"] == "checkpoint"][-1]
     lat, beta, sweep = gpu.load_checkpoint(last["path"])
     assert (beta, sweep) == (6.0, 10)
-    assert abs(gpu.mgq_plaquette(lat) - sweeps[-1]) < 1e-12
+    # the record comes from the plaquette-measuring overrelaxation sweep:
+    # the same field, summed differently (FP32 rounding of Re Tr U A)
+    assert abs(gpu.mgq_plaquette(lat) - sweeps[-1]) < 1e-7

@@ -209,3 +209,28 @@ def test_plaquette_parity(gpu, orc):
     lat = _lat(gpu, dims)
     gpu.mgq_init_links(lat, 0)
     assert gpu.mgq_plaquette(lat) == 1.0
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32c12", 1e-6)])
+@pytest.mark.parametrize("dims", [[6, 4, 4, 10], [8, 8, 8, 8]])
+def test_overrelax_sweep_with_plaquette(gpu, orc, prec, tol, dims):
+    """The overrelaxation sweep that measures the plaquette as it goes leaves
+    the same links as the plain sweep, and its plaquette is the plaquette of
+    those links (FP64: also the oracle's after its own sweep)."""
+    U = orc.init_links(dims, 1, seed=44)
+    orc.update_chain(U, dims, 5.8, 44, 0, 0, 3, 1, 1)
+    a, b = _lat(gpu, dims, prec, seed=44), _lat(gpu, dims, prec, seed=44)
+    a.from_numpy(U)
+    b.from_numpy(U)
+    orc.overrelax_sweep(U, dims)
+    for k in range(2):  # twice in a row: the per-block sums start afresh
+        p = gpu.mgq_overrelax_sweep_plaquette(a)
+        gpu.mgq_overrelax_sweep(b)
+        torch.cuda.synchronize()
+        assert torch.equal(a.links, b.links)
+        ref = gpu.mgq_plaquette(b)
+        assert abs(p - ref) < tol * ref, (p, ref)
+        if k == 0 and prec == "f64":
+            assert abs(p - orc.plaquette(U, dims)) < 1e-12
+    plaq = gpu.mgq_update_sweeps(b, 5.8, 9, 2, 1, 3, plaq_out=True)
+    assert abs(plaq[-1] - gpu.mgq_plaquette(b)) < tol
