@@ -179,7 +179,8 @@ uint64_t mgq_batch_workspace_bytes(const mgq_lattice* lats, int n_lat, int n_swe
  * per launch), so the call can be captured into a CUDA graph.  Results are
  * bit-identical to n_lat separate mgq_update_sweeps calls.  plaq_out
  * (optional, host or device, n_sweeps x n_lat doubles, sweep-major) receives
- * every lattice's FP64 average plaquette after each compound sweep and then
+ * every lattice's FP64 average plaquette after each compound sweep (measured
+ * by the last overrelaxation sweep, as in mgq_update_sweeps) and then
  * needs batch_work (device, 256-B aligned, >= mgq_batch_workspace_bytes).
  * Errors: MGQ_EINVAL (mixed precision, bad beta, ...), MGQ_ENOMEM. */
 mgq_status mgq_update_sweeps_batched(mgq_lattice* lats, int n_lat, const double* betas, uint64_t sweep0,

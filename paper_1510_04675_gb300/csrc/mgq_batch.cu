@@ -89,6 +89,45 @@ __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4) k_overr
     U.store(MU, par, h, u);
 }
 
+// The last overrelaxation sweep's direction-3 sub-sweeps with the plaquette
+// folded in, as in the single-lattice driver: partial sums per block at
+// partials[par * nblocks + blockIdx.x].
+template <class T, int NP>
+__global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4)
+    k_overrelax_batched_last(const __grid_constant__ Batch<T> B, int par, double* __restrict__ partials) {
+    const int l = find_lattice(B, blockIdx.x);
+    const LatDesc<T>& d = B.d[l];
+    const int h = (blockIdx.x - B.prefix[l]) * BATCH_THREADS + threadIdx.x;
+    double acc = 0.0;
+    if (h < d.g.Vh) {
+        const Geom g = geom_of(d);
+        Links<T, NP> U;
+        U.p = d.links;
+        U.S = d.g.S;
+        int x[4];
+        cb_coords(g, par, h, x);
+        const M3<T> A = staple(U, g, x, h, 3, par);
+        M3<T> u = U.load(3, par, h);
+        if (par == 1) acc = (double)retr_nn(u, A);
+        or_link(u, A);
+        U.store(3, par, h, u);
+        acc += site_plaquettes<T, NP, 3>(U, g, par, h);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[par * B.prefix[B.n] + blockIdx.x] = acc;
+}
+
+// one block per lattice: both parities' partials of its blocks, times 1/(18 V)
+template <class T>
+__global__ void k_overrelax_batched_last_final(const __grid_constant__ Batch<T> B, const double* __restrict__ partials,
+                                               double* __restrict__ out) {
+    const int l = blockIdx.x, nb = B.prefix[B.n];
+    double v = 0.0;
+    for (int i = B.prefix[l] + threadIdx.x; i < B.prefix[l + 1]; i += blockDim.x) v += partials[i] + partials[nb + i];
+    v = block_sum(v);
+    if (threadIdx.x == 0) out[l] = v / (18.0 * (double)B.d[l].g.V);
+}
+
 // per-lattice plaquette: blocks of 256 sites, partial sums at the global block index
 template <class T, int NP>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_plaquette_batched(const __grid_constant__ Batch<T> B, double* __restrict__ partials) {
@@ -137,11 +176,14 @@ static void fill_batch(Batch<T>& B, const mgq_lattice* lats, const double* betas
     }
 }
 
+// partial-sum slots: two per 128-site half-lattice block (the plaquette-
+// measuring overrelaxation sub-sweeps), which also covers one per 256-site
+// block (the plaquette kernel)
 uint64_t batch_partials(const mgq_lattice* lats, int n) {
     uint64_t nb = 0;
     for (int i = 0; i < n; i++) {
         const Geom g = make_geom(lats[i].dims);
-        nb += (uint64_t)(g.V + 255) / 256;
+        nb += 2 * (uint64_t)((g.Vh + BATCH_THREADS - 1) / BATCH_THREADS);
     }
     return nb;
 }
@@ -204,16 +246,27 @@ mgq_status mgq_update_sweeps_batched(mgq_lattice* lats, int n_lat, const double*
                                 k_heatbath_batched<T, NP, MU, false><<<nblocks, BATCH_THREADS, 0, st>>>(
                                     Bl, par, (uint32_t)(sweep & 0xffffffffu), (uint32_t)(sweep >> 32), n_hb);
                         });
+                // with a plaquette record, the last overrelaxation sweep's
+                // direction-3 sub-sweeps measure it (per-chunk partials)
+                const bool fold = plaq_out && n_or > 0;
                 for (int k = 0; k < n_or; k++)
                     for (int mu = 0; mu < 4; mu++)
-                        for (int par = 0; par < 2; par++)
+                        for (int par = 0; par < 2; par++) {
+                            if (fold && k == n_or - 1 && mu == 3) {
+                                k_overrelax_batched_last<T, NP><<<nblocks, BATCH_THREADS, 0, st>>>(Bl, par, partials);
+                                continue;
+                            }
                             dispatch_mu(mu, [&]<int MU>() {
                                 k_overrelax_batched<T, NP, MU><<<nblocks, BATCH_THREADS, 0, st>>>(Bl, par);
                             });
+                        }
+                if (fold)
+                    k_overrelax_batched_last_final<T><<<n, 256, 0, st>>>(Bl, partials,
+                                                                         results + (size_t)i * n_lat + first);
             });
             if ((s = cuda_check("mgq_update_sweeps_batched"))) return s;
         }
-        if (plaq_out) {
+        if (plaq_out && n_or == 0) {
             uint64_t poff = 0;
             for (int first = 0; first < n_lat; first += BATCH_CHUNK) {
                 const int n = (n_lat - first < BATCH_CHUNK) ? n_lat - first : BATCH_CHUNK;

@@ -33,10 +33,7 @@ def test_batched_equals_single_runs(gpu, orc, prec):
     for i, (s, b) in enumerate(zip(singles, betas)):
         p = gpu.mgq_update_sweeps(s, b, 7, 3, 1, 2, plaq_out=True)
         assert np.array_equal(s.to_numpy(), lats[i].to_numpy()), i
-        # the single-lattice record comes from the plaquette-measuring
-        # overrelaxation sweep, the batched one from the plaquette kernel:
-        # the same field, summed differently (FP32: rounding of Re Tr U A)
-        assert np.max(np.abs(P[:, i].cpu().numpy() - p)) < (1e-14 if prec == "f64" else 1e-7), i
+        assert np.max(np.abs(P[:, i].cpu().numpy() - p)) < 1e-14, i
 
 
 def test_batched_matches_oracle_fp64(gpu, orc):
@@ -72,7 +69,7 @@ def test_batched_graph_capture(gpu, orc):
     for i, b in enumerate(betas):
         p = gpu.mgq_update_sweeps(singles[i], b, 1, 1, 1, 1, plaq_out=True)
         assert np.array_equal(singles[i].to_numpy(), lats[i].to_numpy()), i
-        assert abs(P[0, i].item() - p[0]) < 1e-7  # FP32: summed differently, as above
+        assert abs(P[0, i].item() - p[0]) < 1e-14
 
 
 def test_batched_rejects_mixed_precision(gpu):
