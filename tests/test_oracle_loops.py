@@ -73,3 +73,31 @@ def test_loops_gauge_invariant_and_h(orc):
     a, b = orc.partial_loops(U, dims), orc.partial_loops(Ug, dims)
     assert np.max(np.abs(a - b)) < 1e-13
     assert 0 < a[8] <= 6.0
+
+
+def test_plaquette_sum_from_odd_time_links_and_spatial_planes(orc):
+    """The decomposition the plaquette-measuring overrelaxation sweep relies
+    on (Sec. III plaquette, Sec. IV.A overrelaxation): the plaquettes of the
+    planes (3, nu) are the staple products Re Tr(U_3(x) A_3(x)) of the odd
+    sites, each counted once, and overrelaxation keeps each such product."""
+    dims = [4, 2, 4, 6]
+    U = orc.init_links(dims, 1, seed=21)
+    V = U.shape[0]
+    total = orc.plaquette(U, dims) * 18 * V
+    spatial = 0.0
+    for s in range(V):
+        x = orc.coords(dims, s)
+        for mu in range(3):
+            for nu in range(mu + 1, 3):
+                xm = list(x); xm[mu] = (xm[mu] + 1) % dims[mu]
+                xn = list(x); xn[nu] = (xn[nu] + 1) % dims[nu]
+                P = U[s, mu] @ U[orc.site_index(dims, xm), nu] @ U[orc.site_index(dims, xn), mu].conj().T @ U[s, nu].conj().T
+                spatial += P.trace().real
+    odd = [s for s in range(V) if sum(orc.coords(dims, s)) % 2 == 1]
+    timelike = sum((U[s, 3] @ orc.staple(U, dims, s, 3)).trace().real for s in odd)
+    assert abs(spatial + timelike - total) < 1e-10 * max(1.0, abs(total))
+    # overrelaxation of one link leaves its staple product unchanged
+    s = odd[3]
+    A = orc.staple(U, dims, s, 3)
+    new = orc.overrelax_one_link(U, dims, s, 3)
+    assert abs((new @ A).trace().real - (U[s, 3] @ A).trace().real) < 1e-12
