@@ -235,10 +235,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4) k_heatbath(Links<
         n_hb = 1;
         dec = nullptr;
     }
+    pdl_launch_dependents();
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= g.Vh) return;
     int x[4];
     cb_coords(g, par, h, x);
+    pdl_wait();
+    if (h >= g.Vh) return;
     const M3<T> A = staple(U, g, x, h, MU, par);
     M3<T> u = U.load(MU, par, h);
     const int lex = lex_of(g, x);
@@ -248,10 +250,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4) k_heatbath(Links<
 
 template <class T, int NP, int MU>
 __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4) k_overrelax(Links<T, NP> U, Geom g, int par) {
+    pdl_launch_dependents();
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= g.Vh) return;
     int x[4];
     cb_coords(g, par, h, x);
+    pdl_wait();
+    if (h >= g.Vh) return;
     const M3<T> A = staple(U, g, x, h, MU, par);
     M3<T> u = U.load(MU, par, h);
     or_link(u, A);
@@ -269,11 +273,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4) k_overrelax(Links
 template <class T, int NP>
 __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4)
     k_overrelax_last(Links<T, NP> U, Geom g, int par, double* __restrict__ partials) {
+    pdl_launch_dependents();
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     double acc = 0.0;
+    int x[4];
+    cb_coords(g, par, h, x);
+    pdl_wait();
     if (h < g.Vh) {
-        int x[4];
-        cb_coords(g, par, h, x);
         const M3<T> A = staple(U, g, x, h, 3, par);
         M3<T> u = U.load(3, par, h);
         if (par == 1) acc = (double)retr_nn(u, A);
@@ -343,6 +349,22 @@ __global__ void k_final_max(const double* __restrict__ partials, int n, double* 
 // =============================================================== launchers
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
+// launch with programmatic stream serialisation (see pdl_wait)
+template <class... KArgs, class... Args>
+static void launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, (KArgs)args...);
+}
+
 // Launch shape of the sub-sweep kernels per (kernel, precision): threads per
 // block, at most the 128 the kernels are compiled for.  Set by
 // mgq_set_block_size (the autotuner); 128 by default.
@@ -357,11 +379,11 @@ mgq_status heatbath_subsweep(mgq_lattice* lat, double beta, uint64_t sweep, int 
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
         dispatch_mu(mu, [&]<int MU>() {
             if (n_hb == 1 && !dec)
-                k_heatbath<T, NP, MU, true><<<nblk(g.Vh, bs), bs, 0, st>>>(links_of<T, NP>(lat), g, par, (T)beta, rk,
-                                                                           n_hb, dec);
+                launch_pdl(k_heatbath<T, NP, MU, true>, nblk(g.Vh, bs), bs, st, links_of<T, NP>(lat), g, par,
+                           (T)beta, rk, n_hb, dec);
             else
-                k_heatbath<T, NP, MU, false><<<nblk(g.Vh, bs), bs, 0, st>>>(links_of<T, NP>(lat), g, par, (T)beta, rk,
-                                                                            n_hb, dec);
+                launch_pdl(k_heatbath<T, NP, MU, false>, nblk(g.Vh, bs), bs, st, links_of<T, NP>(lat), g, par,
+                           (T)beta, rk, n_hb, dec);
         });
     });
     return cuda_check("mgq_heatbath");
@@ -373,7 +395,7 @@ mgq_status overrelax_subsweep(mgq_lattice* lat, int mu, int par, cudaStream_t st
     const int bs = g_block[MGQ_KERNEL_OVERRELAX][lat->prec];
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
         dispatch_mu(mu, [&]<int MU>() {
-            k_overrelax<T, NP, MU><<<nblk(g.Vh, bs), bs, 0, st>>>(links_of<T, NP>(lat), g, par);
+            launch_pdl(k_overrelax<T, NP, MU>, nblk(g.Vh, bs), bs, st, links_of<T, NP>(lat), g, par);
         });
     });
     return cuda_check("mgq_overrelax");
@@ -393,7 +415,7 @@ mgq_status overrelax_sweep_plaquette(mgq_lattice* lat, double* dev_out, cudaStre
     double* partials = reinterpret_cast<double*>(ws_alg(lat));  // free during sweeps; >= 2 nb doubles
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
         for (int par = 0; par < 2; par++)
-            k_overrelax_last<T, NP><<<nb, bs, 0, st>>>(links_of<T, NP>(lat), g, par, partials + par * nb);
+            launch_pdl(k_overrelax_last<T, NP>, nb, bs, st, links_of<T, NP>(lat), g, par, partials + par * nb);
     });
     launch_final_sum(partials, 2 * nb, 1.0 / (18.0 * (double)g.V), dev_out, st);
     return cuda_check("overrelax_sweep_plaquette");

@@ -335,6 +335,15 @@ __device__ __forceinline__ int lex_hop(const Geom& g, const int x[4], int mu, in
     return lex_of(g, y);
 }
 
+// ----------------------------------------------------------------- launch overlap
+// Programmatic dependent launch: a sub-sweep launched with the programmatic
+// stream-serialisation attribute may start while the previous kernel drains;
+// it lets its own successor start likewise, does its index arithmetic, and
+// waits for the previous kernel's completion (and memory) before it reads
+// any link.  Without the attribute both instructions do nothing.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ----------------------------------------------------------------- fields
 // read-only cached load of one complex element
 __device__ __forceinline__ Cx<double> ldg_cx(const Cx<double>* p) {
