@@ -349,22 +349,6 @@ __global__ void k_final_max(const double* __restrict__ partials, int n, double* 
 // =============================================================== launchers
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
-// launch with programmatic stream serialisation (see pdl_wait)
-template <class... KArgs, class... Args>
-static void launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, (KArgs)args...);
-}
-
 // Launch shape of the sub-sweep kernels per (kernel, precision): threads per
 // block, at most the 128 the kernels are compiled for.  Set by
 // mgq_set_block_size (the autotuner); 128 by default.

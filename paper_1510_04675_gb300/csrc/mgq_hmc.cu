@@ -15,12 +15,14 @@ namespace mgq {
 // directions while they are still in cache.
 template <class T, int NP>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_force(Links<T, NP> U, Geom g, Alg<T> B, T coef, T alpha) {
+    pdl_launch_dependents();
     const int w = threadIdx.x >> 5;
     const int mu = w >> 1, par = w & 1;
     const int h = blockIdx.x * 32 + (threadIdx.x & 31);
-    if (h >= g.Vh) return;
     int x[4];
     cb_coords(g, par, h, x);
+    pdl_wait();
+    if (h >= g.Vh) return;
     const M3<T> A = staple(U, g, x, h, mu, par);
     const M3<T> M = mul_nn(U.load(mu, par, h), A);
     T t[8];
@@ -38,6 +40,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_force(Links<T, 
 // U <- exp(s B) U on every link; the FP32 formats are reunitarised.
 template <class T, int NP>
 __global__ void __launch_bounds__(128) k_exp_update(Links<T, NP> U, Geom g, Alg<T> B, T s) {
+    pdl_launch_dependents();
+    pdl_wait();
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 8 * g.Vh) return;
     const int mp = idx / g.Vh, h = idx - mp * g.Vh, mu = mp >> 1, par = mp & 1;
@@ -129,8 +133,8 @@ static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 mgq_status force_accumulate(const mgq_lattice* lat, void* B, double coef, double alpha, cudaStream_t st) {
     const Geom g = make_geom(lat->dims);
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
-        k_force<T, NP><<<nblk(g.Vh, 32), 256, 0, st>>>(links_of<T, NP>(lat), g, alg_at<T>(B, lat->dims), (T)coef,
-                                                             (T)alpha);
+        launch_pdl(k_force<T, NP>, nblk(g.Vh, 32), 256, st, links_of<T, NP>(lat), g, alg_at<T>(B, lat->dims),
+                   (T)coef, (T)alpha);
     });
     return cuda_check("force");
 }
@@ -138,8 +142,8 @@ mgq_status force_accumulate(const mgq_lattice* lat, void* B, double coef, double
 mgq_status exp_update(const mgq_lattice* lat, void* B, double s, cudaStream_t st) {
     const Geom g = make_geom(lat->dims);
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
-        k_exp_update<T, NP><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(links_of<T, NP>(lat), g, alg_at<T>(B, lat->dims),
-                                                                  (T)s);
+        launch_pdl(k_exp_update<T, NP>, nblk(8L * g.Vh, 128), 128, st, links_of<T, NP>(lat), g,
+                   alg_at<T>(B, lat->dims), (T)s);
     });
     return cuda_check("exp_update");
 }
