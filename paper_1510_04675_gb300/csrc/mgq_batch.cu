@@ -51,9 +51,11 @@ template <class T, int NP, int MU, bool NHB1>
 __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4)
     k_heatbath_batched(const __grid_constant__ Batch<T> B, int par, uint32_t idx_lo, uint32_t idx_hi, int n_hb) {
     if constexpr (NHB1) n_hb = 1;
+    pdl_launch_dependents();
     const int l = find_lattice(B, blockIdx.x);
     const LatDesc<T>& d = B.d[l];
     const int h = (blockIdx.x - B.prefix[l]) * BATCH_THREADS + threadIdx.x;
+    pdl_wait();
     if (h >= d.g.Vh) return;
     const Geom g = geom_of(d);
     Links<T, NP> U;
@@ -73,9 +75,11 @@ __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4)
 
 template <class T, int NP, int MU>
 __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4) k_overrelax_batched(const __grid_constant__ Batch<T> B, int par) {
+    pdl_launch_dependents();
     const int l = find_lattice(B, blockIdx.x);
     const LatDesc<T>& d = B.d[l];
     const int h = (blockIdx.x - B.prefix[l]) * BATCH_THREADS + threadIdx.x;
+    pdl_wait();
     if (h >= d.g.Vh) return;
     const Geom g = geom_of(d);
     Links<T, NP> U;
@@ -95,9 +99,11 @@ __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4) k_overr
 template <class T, int NP>
 __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4)
     k_overrelax_batched_last(const __grid_constant__ Batch<T> B, int par, double* __restrict__ partials) {
+    pdl_launch_dependents();
     const int l = find_lattice(B, blockIdx.x);
     const LatDesc<T>& d = B.d[l];
     const int h = (blockIdx.x - B.prefix[l]) * BATCH_THREADS + threadIdx.x;
+    pdl_wait();
     double acc = 0.0;
     if (h < d.g.Vh) {
         const Geom g = geom_of(d);
@@ -240,11 +246,11 @@ mgq_status mgq_update_sweeps_batched(mgq_lattice* lats, int n_lat, const double*
                     for (int par = 0; par < 2; par++)
                         dispatch_mu(mu, [&]<int MU>() {
                             if (n_hb == 1)
-                                k_heatbath_batched<T, NP, MU, true><<<nblocks, BATCH_THREADS, 0, st>>>(
-                                    Bl, par, (uint32_t)(sweep & 0xffffffffu), (uint32_t)(sweep >> 32), n_hb);
+                                launch_pdl(k_heatbath_batched<T, NP, MU, true>, nblocks, BATCH_THREADS, st, Bl, par,
+                                           (uint32_t)(sweep & 0xffffffffu), (uint32_t)(sweep >> 32), n_hb);
                             else
-                                k_heatbath_batched<T, NP, MU, false><<<nblocks, BATCH_THREADS, 0, st>>>(
-                                    Bl, par, (uint32_t)(sweep & 0xffffffffu), (uint32_t)(sweep >> 32), n_hb);
+                                launch_pdl(k_heatbath_batched<T, NP, MU, false>, nblocks, BATCH_THREADS, st, Bl, par,
+                                           (uint32_t)(sweep & 0xffffffffu), (uint32_t)(sweep >> 32), n_hb);
                         });
                 // with a plaquette record, the last overrelaxation sweep's
                 // direction-3 sub-sweeps measure it (per-chunk partials)
@@ -253,11 +259,11 @@ mgq_status mgq_update_sweeps_batched(mgq_lattice* lats, int n_lat, const double*
                     for (int mu = 0; mu < 4; mu++)
                         for (int par = 0; par < 2; par++) {
                             if (fold && k == n_or - 1 && mu == 3) {
-                                k_overrelax_batched_last<T, NP><<<nblocks, BATCH_THREADS, 0, st>>>(Bl, par, partials);
+                                launch_pdl(k_overrelax_batched_last<T, NP>, nblocks, BATCH_THREADS, st, Bl, par, partials);
                                 continue;
                             }
                             dispatch_mu(mu, [&]<int MU>() {
-                                k_overrelax_batched<T, NP, MU><<<nblocks, BATCH_THREADS, 0, st>>>(Bl, par);
+                                launch_pdl(k_overrelax_batched<T, NP, MU>, nblocks, BATCH_THREADS, st, Bl, par);
                             });
                         }
                 if (fold)
