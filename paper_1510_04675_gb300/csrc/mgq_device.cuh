@@ -345,13 +345,18 @@ __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepc
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // ----------------------------------------------------------------- fields
-// read-only cached load of one complex element
+// load of one complex element.  A plain (coherent) global load, not the
+// read-only path: kernels launched with programmatic dependent launch start
+// before their predecessor has finished writing the links, and the
+// read-only path is specified only for data that no one writes during the
+// reading kernel's lifetime; the plain load after griddepcontrol.wait is
+// ordered after those writes by the memory model.
 __device__ __forceinline__ Cx<double> ldg_cx(const Cx<double>* p) {
-    double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    double2 v = *reinterpret_cast<const double2*>(p);
     return mk(v.x, v.y);
 }
 __device__ __forceinline__ Cx<float> ldg_cx(const Cx<float>* p) {
-    float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    float2 v = *reinterpret_cast<const float2*>(p);
     return mk(v.x, v.y);
 }
 

@@ -10,7 +10,9 @@
 // The controller lives on the device: each trial is a fixed sequence of
 // launches whose kernels read the step size and their gate from a small
 // control block, so the host never waits on a step.  It reads the finished
-// flag once per chunk of trials.
+// flag once per chunk of trials.  The trial's kernels use programmatic
+// dependent launch (see pdl_wait), so they read their predecessors' outputs
+// with plain loads only.
 #include "mgq_internal.h"
 #include "mgq_stencil.cuh"
 
@@ -45,6 +47,8 @@ __global__ void k_adapt_init(FlowCtl* c, double eps0) {
 }
 
 __global__ void k_adapt_begin(FlowCtl* c, double t_end, double eps_max, double dt_meas, int max_meas) {
+    pdl_launch_dependents();
+    pdl_wait();
     c->active = 0;
     c->restore = 0;
     c->meas = 0;
@@ -69,6 +73,8 @@ __global__ void k_adapt_begin(FlowCtl* c, double t_end, double eps_max, double d
 }
 
 __global__ void k_adapt_end(FlowCtl* c, double tol, double eps_max) {
+    pdl_launch_dependents();
+    pdl_wait();
     if (!c->active) return;
     const double d = __longlong_as_double((long long)c->dbits);
     double fac = d > 0.0 ? 0.95 * cbrt(tol / d) : 2.0;
@@ -93,8 +99,10 @@ __global__ void k_adapt_end(FlowCtl* c, double tol, double eps_max) {
 // all eight (mu, parity) planes.
 template <class T, int NP>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2)
-    k_flow_stage(Links<T, NP> U, Geom g, Alg<T> B, Alg<T> Y, const FlowCtl* __restrict__ c, T cB, T aB, T cY, T aY) {
-    if (!__ldg(&c->active)) return;
+    k_flow_stage(Links<T, NP> U, Geom g, Alg<T> B, Alg<T> Y, const FlowCtl* c, T cB, T aB, T cY, T aY) {
+    pdl_launch_dependents();
+    pdl_wait();
+    if (!c->active) return;
     const int w = threadIdx.x >> 5;
     const int mu = w >> 1, par = w & 1;
     const int h = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -104,7 +112,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2)
     const M3<T> A = staple(U, g, x, h, mu, par);
     T t[8];
     ta_coeffs(mul_nn(U.load(mu, par, h), A), t);
-    const T mh = (T)(-__ldg(&c->h));
+    const T mh = (T)(-c->h);
     T* b = B.at(mu, par, h);
 #pragma unroll
     for (int a = 0; a < 8; a++) {
@@ -124,9 +132,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2)
 // W <- exp(s B) W; with backup, the old W is saved there first (the start
 // of the trial, restored on rejection).
 template <class T, int NP>
-__global__ void __launch_bounds__(128) k_flow_exp(Links<T, NP> U, Geom g, Alg<T> B, T s, const FlowCtl* __restrict__ c,
+__global__ void __launch_bounds__(128) k_flow_exp(Links<T, NP> U, Geom g, Alg<T> B, T s, const FlowCtl* c,
                                                   Links<T, NP> backup, int save) {
-    if (!__ldg(&c->active)) return;
+    pdl_launch_dependents();
+    pdl_wait();
+    if (!c->active) return;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 8 * g.Vh) return;
     const int mp = idx / g.Vh, h = idx - mp * g.Vh, mu = mp >> 1, par = mp & 1;
@@ -144,8 +154,10 @@ __global__ void __launch_bounds__(128) k_flow_exp(Links<T, NP> U, Geom g, Alg<T>
 // d = max over links of |W3 - exp(Y) W0|_F / 3, Y = 2 Z1 - Z0.
 template <class T, int NP>
 __global__ void __launch_bounds__(128) k_flow_error(Links<T, NP> U, Links<T, NP> U0, Geom g, Alg<T> Y,
-                                                    FlowCtl* __restrict__ c) {
-    if (!__ldg(&c->active)) return;
+                                                    FlowCtl* c) {
+    pdl_launch_dependents();
+    pdl_wait();
+    if (!c->active) return;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     double d = 0.0;
     if (idx < 8 * g.Vh) {
@@ -178,15 +190,19 @@ __global__ void __launch_bounds__(128) k_flow_error(Links<T, NP> U, Links<T, NP>
     if ((threadIdx.x & 31) == 0 && bits) atomicMax(&c->dbits, bits);
 }
 
-__global__ void k_flow_restore(uint4* __restrict__ links, const uint4* __restrict__ backup, size_t nwords,
-                               const FlowCtl* __restrict__ c) {
-    if (!__ldg(&c->restore)) return;
+__global__ void k_flow_restore(uint4* links, const uint4* backup, size_t nwords,
+                               const FlowCtl* c) {
+    pdl_launch_dependents();
+    pdl_wait();
+    if (!c->restore) return;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nwords; i += (size_t)gridDim.x * blockDim.x)
         links[i] = backup[i];
 }
 
 // meas[2m] = E (site average), meas[2m+1] = Q from the clover partials; m++.
-__global__ void k_adapt_meas(FlowCtl* c, const double* __restrict__ partials, int nb, double invV, double* meas) {
+__global__ void k_adapt_meas(FlowCtl* c, const double* partials, int nb, double invV, double* meas) {
+    pdl_launch_dependents();
+    pdl_wait();
     if (!c->meas) return;
     double e = 0.0, q = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
@@ -256,28 +272,28 @@ mgq_status mgq_wilson_flow_adaptive(mgq_lattice* lat, double t_end, double tol, 
 
     auto measure = [&]() {
         const int nb = clover_partials(lat, partials, &c->meas, st);
-        k_adapt_meas<<<1, 512, 0, st>>>(c, partials, nb, invV, meas);
+        launch_pdl(k_adapt_meas, 1, 512, st, c, partials, nb, invV, meas);
     };
     auto trial = [&]() {
-        k_adapt_begin<<<1, 1, 0, st>>>(c, t_end, eps_max, dt_meas, nm);
+        launch_pdl(k_adapt_begin, 1, 1, st, c, t_end, eps_max, dt_meas, nm);
         dispatch_prec(lat->prec, [&]<class T, int NP>() {
             const Links<T, NP> U = links_of<T, NP>(lat), U0 = links_at<T, NP>(backup, lat->dims);
             const Alg<T> B = alg_at<T>(Bp, lat->dims), Y = alg_at<T>(scratch, lat->dims);
             const int fb = nblk(g.Vh, 32), eb = nblk(8L * g.Vh, 128);
             // Z0: B = Z0, Y = -Z0
-            k_flow_stage<T, NP><<<fb, 256, 0, st>>>(U, g, B, Y, c, T(1), T(0), T(-1), T(0));
-            k_flow_exp<T, NP><<<eb, 128, 0, st>>>(U, g, B, T(0.25), c, U0, 1);
+            launch_pdl(k_flow_stage<T, NP>, fb, 256, st, U, g, B, Y, c, T(1), T(0), T(-1), T(0));
+            launch_pdl(k_flow_exp<T, NP>, eb, 128, st, U, g, B, T(0.25), c, U0, 1);
             // Z1: B = 8/9 Z1 - 17/36 B, Y = 2 Z1 + Y
-            k_flow_stage<T, NP><<<fb, 256, 0, st>>>(U, g, B, Y, c, T(8.0 / 9.0), T(-17.0 / 36.0), T(2), T(1));
-            k_flow_exp<T, NP><<<eb, 128, 0, st>>>(U, g, B, T(1), c, U0, 0);
+            launch_pdl(k_flow_stage<T, NP>, fb, 256, st, U, g, B, Y, c, T(8.0 / 9.0), T(-17.0 / 36.0), T(2), T(1));
+            launch_pdl(k_flow_exp<T, NP>, eb, 128, st, U, g, B, T(1), c, U0, 0);
             // Z2: B = 3/4 Z2 - B
-            k_flow_stage<T, NP><<<fb, 256, 0, st>>>(U, g, B, Y, c, T(0.75), T(-1), T(0), T(0));
-            k_flow_exp<T, NP><<<eb, 128, 0, st>>>(U, g, B, T(1), c, U0, 0);
-            k_flow_error<T, NP><<<eb, 128, 0, st>>>(U, U0, g, Y, c);
+            launch_pdl(k_flow_stage<T, NP>, fb, 256, st, U, g, B, Y, c, T(0.75), T(-1), T(0), T(0));
+            launch_pdl(k_flow_exp<T, NP>, eb, 128, st, U, g, B, T(1), c, U0, 0);
+            launch_pdl(k_flow_error<T, NP>, eb, 128, st, U, U0, g, Y, c);
         });
-        k_adapt_end<<<1, 1, 0, st>>>(c, tol, eps_max);
-        k_flow_restore<<<1184, 256, 0, st>>>(reinterpret_cast<uint4*>(lat->links),
-                                             reinterpret_cast<const uint4*>(backup), nwords, c);
+        launch_pdl(k_adapt_end, 1, 1, st, c, tol, eps_max);
+        launch_pdl(k_flow_restore, 1184, 256, st, reinterpret_cast<uint4*>(lat->links),
+                   reinterpret_cast<const uint4*>(backup), nwords, (const FlowCtl*)c);
         measure();
     };
 
