@@ -76,6 +76,7 @@ _SIGS = {
     "orc_transfer": (None, [_D, _I, _D]),
     "orc_partial_action": (_dbl, [_D, _I, _int]),
     "orc_prolongate": (None, [_D, _I, _D, _dbl, _dbl, _int, _int, _I, _D]),
+    "orc_ape_step": (None, [_D, _I, _int, _dbl, _int]),
     "orc_flow_step": (None, [_D, _I, _dbl]),
     "orc_wilson_loop": (_dbl, [_D, _I, _int, _int]),
     "orc_partial_loops": (None, [_D, _I, _D]),
@@ -340,6 +341,13 @@ def transfer(Uc, dims_c) -> np.ndarray:
 
 def partial_action(U, dims, d) -> float:
     return float(lib().orc_partial_action(_dp(U.view(np.float64)), _dims(dims), int(d)))
+
+
+def ape_step(U, dims, d, c=0.05, n_pass=8) -> np.ndarray:
+    """One Jacobi APE step of interpolation stage d on a copy of U (Eq. APE)."""
+    W = np.ascontiguousarray(U.copy())
+    lib().orc_ape_step(_dp(W.view(np.float64)), _dims(dims), int(d), float(c), int(n_pass))
+    return W
 
 
 def prolongate(Uc, dims_c, c=0.05, rel_tol=1e-5, max_iter=10000, n_pass=8):

@@ -1035,6 +1035,15 @@ static void ape_step(double* U, double* Unew, const lat_t* g, int d, double c, i
     memcpy(U, Unew, sizeof(double) * nU);
 }
 
+/* One APE step of stage d on the field U in place (exposed for the pins). */
+void orc_ape_step(double* U, const int* dims, int d, double c, int n_pass)
+{
+    lat_t g = make_lat(dims);
+    double* tmp = malloc(sizeof(double) * g.V * 72);
+    ape_step(U, tmp, &g, d, c, n_pass);
+    free(tmp);
+}
+
 /*
  * Prolongation = transfer, then interpolation stages d = 0, 1, 2 in order;
  * each stage repeats APE steps until the relative change of S_d between
