@@ -81,6 +81,8 @@ _SIGS = {
     "orc_wilson_loop": (_dbl, [_D, _I, _int, _int]),
     "orc_partial_loops": (None, [_D, _I, _D]),
     "orc_clover_EQ": (None, [_D, _I, _D, _D]),
+    "orc_clover_q_site": (_dbl, [_D, _I, _long, _int]),
+    "orc_topo_charge_improved": (None, [_D, _I, _D]),
     "orc_wilson_flow": (None, [_D, _I, _dbl, _int, _int, _D, _D]),
     "orc_flow_trial_step": (_dbl, [_D, _I, _dbl]),
     "orc_wilson_flow_adaptive": (_int, [_D, _I, _dbl, _dbl, _dbl, _dbl, _dbl, _D, _D, _int, _I, _I]),
@@ -370,6 +372,19 @@ def clover_EQ(U, dims):
     Q = ctypes.c_double()
     lib().orc_clover_EQ(_dp(U.view(np.float64)), _dims(dims), ctypes.byref(E), ctypes.byref(Q))
     return float(E.value), float(Q.value)
+
+
+def clover_q_site(U, dims, s, m) -> float:
+    """Clover charge density at site s from the m x m leaves (no 1/m^4); m = 0:
+    the three-loop improved density."""
+    return float(lib().orc_clover_q_site(_dp(U.view(np.float64)), _dims(dims), int(s), int(m)))
+
+
+def topo_charge_improved(U, dims) -> np.ndarray:
+    """[Q_improved, Q_1x1, Q_2x2, Q_3x3] (Sec. IV.C, three-loop improved charge)."""
+    out = np.zeros(4)
+    lib().orc_topo_charge_improved(_dp(U.view(np.float64)), _dims(dims), _dp(out))
+    return out
 
 
 def wilson_flow(W, dims, eps, n_steps, meas_every):
