@@ -231,6 +231,16 @@ mgq_status mgq_partial_loops(const mgq_lattice* lat, double* out, void* stream);
  * E_out, Q_out: one double each (either may be NULL), host or device. */
 mgq_status mgq_topo_charge(const mgq_lattice* lat, double* E_out, double* Q_out, void* stream);
 
+/* Three-loop improved topological charge (Sec. IV.C, the gluonic operator of
+ * de Forcrand, Garcia Perez and Stamatescu, Nucl. Phys. B 499 (1997) 409):
+ * Q_m = sum_x q_m(x) with q_m the clover density above built from the four
+ * m x m leaves of every plane (m = 1, 2, 3), and
+ * Q = 3/2 Q_1 - 3/5 Q_2 / 2^4 + 1/10 Q_3 / 3^4, the tree-level coefficients
+ * that cancel the O(a^2) and O(a^4) terms of the m x m clovers.
+ * Q_out[4] = {Q, Q_1, Q_2, Q_3} (host or device).  Needs the workspace.
+ * Errors: MGQ_EINVAL, MGQ_ENOMEM. */
+mgq_status mgq_topo_charge_improved(const mgq_lattice* lat, double* Q_out, void* stream);
+
 /* Wilson flow with fixed step eps (Sec. IV.B), Luscher's third-order
  * Runge-Kutta scheme with generator Z(W) = -TA(W A(W)); n_steps steps, the
  * links are replaced by the flowed field.  E and Q (as mgq_topo_charge) are
@@ -239,6 +249,18 @@ mgq_status mgq_topo_charge(const mgq_lattice* lat, double* E_out, double* Q_out,
  * skip).  Uses the workspace's algebra buffer.  Errors: MGQ_EINVAL, MGQ_ENOMEM. */
 mgq_status mgq_wilson_flow(mgq_lattice* lat, double eps, int n_steps, int meas_every, double* E_out,
                            double* Q_out, void* stream);
+
+/* Wilson flow to t_end in the form of the problem statement: fixed steps of
+ * size eps (Sec. IV.B, the RK3 step above), except that a step that would pass
+ * the next measurement time, or t_end, is shortened to end on it.  E (clover)
+ * and Q are measured at the n_meas flow times t_meas[] (host, ascending, each
+ * in [0, t_end]; at most 224) into E_out[i], Q_out[i] (host or device, NULL to
+ * skip).  charge 0: clover Q; charge 1: the three-loop improved Q of
+ * mgq_topo_charge_improved (Sec. IV.C).  The links are replaced by the field
+ * at t_end.  Uses the workspace's algebra buffer.  Errors: MGQ_EINVAL (bad
+ * times, eps <= 0, more than 1e8 steps), MGQ_ENOMEM. */
+mgq_status mgq_wilson_flow_times(mgq_lattice* lat, double t_end, double eps, const double* t_meas, int n_meas,
+                                 int charge, double* E_out, double* Q_out, void* stream);
 
 /* Adaptive-step Wilson flow (Sec. IV.B, Table II: tolerance 0.01, maximal
  * step 0.2, measurements every t0/4).  Each trial step of size h runs the
@@ -278,6 +300,16 @@ int mgq_flow_adaptive_measurements(double t_end, double dt_meas);
 /* Bytes of the caller scratch of mgq_wilson_flow_step_adjoint (2 link fields
  * + 7 algebra fields); 0 on invalid extents or precision. */
 uint64_t mgq_flow_adjoint_scratch_bytes(const mgq_lattice* lat);
+
+/* g_out = J(omega)^T g_in: pulls a cotangent g_in at the field exp(omega) U back
+ * to the algebra variable omega, J(X)^T = sum_n (-ad_X)^n / (n+1)! the adjoint
+ * of the differential of exp (d/dt e^{X + tY} e^{-X} = sum_n ad_X^n Y/(n+1)!).
+ * With it a function of exp(omega) U gets its true omega-derivative, not only
+ * the Lie derivative at omega = 0 (the exponential of the HMC Q-step, Sec. IV.D,
+ * and of every RK3 stage, Sec. IV.B, have this differential).  omega, g_in,
+ * g_out: device algebra fields in the mom layout and precision (g_in may equal
+ * g_out).  Errors: MGQ_EINVAL (NULL or misaligned pointers, bad lattice). */
+mgq_status mgq_exp_vjp(const mgq_lattice* lat, const void* omega, const void* g_in, void* g_out, void* stream);
 
 /* lambda += scale * DZ(W)^T [psi]: the vector-Jacobian product of the flow
  * generator Z(W) = -TA(W A(W)) at W = lat->links (all device, mom layout). */

@@ -83,6 +83,7 @@ _SIGS = {
     "orc_clover_EQ": (None, [_D, _I, _D, _D]),
     "orc_clover_q_site": (_dbl, [_D, _I, _long, _int]),
     "orc_topo_charge_improved": (None, [_D, _I, _D]),
+    "orc_wilson_flow_times": (None, [_D, _I, _dbl, _dbl, _D, _int, _int, _D, _D]),
     "orc_wilson_flow": (None, [_D, _I, _dbl, _int, _int, _D, _D]),
     "orc_flow_trial_step": (_dbl, [_D, _I, _dbl]),
     "orc_wilson_flow_adaptive": (_int, [_D, _I, _dbl, _dbl, _dbl, _dbl, _dbl, _D, _D, _int, _I, _I]),
@@ -385,6 +386,16 @@ def topo_charge_improved(U, dims) -> np.ndarray:
     out = np.zeros(4)
     lib().orc_topo_charge_improved(_dp(U.view(np.float64)), _dims(dims), _dp(out))
     return out
+
+
+def wilson_flow_times(W, dims, t_end, eps, t_meas, charge=0):
+    """Flow W in place to t_end (steps eps, shortened to land on each t_meas);
+    returns E, Q at t_meas (charge 0: clover Q, 1: improved Q)."""
+    tm = np.ascontiguousarray(np.asarray(t_meas, dtype=np.float64))
+    E, Q = np.zeros(tm.size), np.zeros(tm.size)
+    lib().orc_wilson_flow_times(_dp(W.view(np.float64)), _dims(dims), float(t_end), float(eps), _dp(tm), int(tm.size),
+                                int(charge), _dp(E), _dp(Q))
+    return E, Q
 
 
 def wilson_flow(W, dims, eps, n_steps, meas_every):

@@ -1380,6 +1380,36 @@ void orc_topo_charge_improved(const double* U, const int* dims, double* out)
 }
 
 /*
+ * Wilson flow from t = 0 to t_end in steps of eps, a step that would pass the
+ * next measurement time (or t_end) being shortened to end on it; E (clover)
+ * and Q (charge 0: clover, 1: three-loop improved) at the ascending times
+ * t_meas[0..n_meas-1] in [0, t_end].
+ */
+void orc_wilson_flow_times(double* W, const int* dims, double t_end, double eps, const double* t_meas, int n_meas,
+                           int charge, double* E_out, double* Q_out)
+{
+    const double tiny = 1e-12 * (t_end > 1.0 ? t_end : 1.0);
+    double t = 0.0;
+    int i = 0;
+    for (;;) {
+        while (i < n_meas && t_meas[i] <= t + tiny) {
+            orc_clover_EQ(W, dims, &E_out[i], &Q_out[i]);
+            if (charge == 1) {
+                double q4[4];
+                orc_topo_charge_improved(W, dims, q4);
+                Q_out[i] = q4[0];
+            }
+            i++;
+        }
+        if (!(t < t_end - tiny)) break;
+        double stop = (i < n_meas && t_meas[i] < t_end) ? t_meas[i] : t_end;
+        double h = (stop - t < eps) ? stop - t : eps;
+        orc_flow_step(W, dims, h);
+        t = (h == stop - t) ? stop : t + h;
+    }
+}
+
+/*
  * Wilson flow of n_steps steps of size eps; E and Q measured at flow times
  * t = k eps for k = 0, meas_every, 2 meas_every, ... <= n_steps.
  */

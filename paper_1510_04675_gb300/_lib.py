@@ -62,6 +62,8 @@ SIGNATURES = {
     "mgq_plaquette": (_st, [_P, _vp, _vp]),
     "mgq_plaquette_noalloc": (_st, [_P, _vp, _vp]),
     "mgq_topo_charge": (_st, [_P, _vp, _vp, _vp]),
+    "mgq_topo_charge_improved": (_st, [_P, _vp, _vp]),
+    "mgq_wilson_flow_times": (_st, [_P, _d, _d, _vp, _i, _i, _vp, _vp, _vp]),
     "mgq_wilson_loop": (_st, [_P, _i, _i, _vp, _vp]),
     "mgq_partial_loops": (_st, [_P, _vp, _vp]),
     "mgq_wilson_flow": (_st, [_P, _d, _i, _i, _vp, _vp, _vp]),
@@ -72,6 +74,7 @@ SIGNATURES = {
     "mgq_link_exp_update": (_st, [_P, _vp, _d, _vp]),
     "mgq_flow_adjoint_scratch_bytes": (ctypes.c_uint64, [_P]),
     "mgq_flow_vjp": (_st, [_P, _vp, _d, _vp, _vp]),
+    "mgq_exp_vjp": (_st, [_P, _vp, _vp, _vp, _vp]),
     "mgq_wilson_flow_step_adjoint": (_st, [_P, _d, _vp, _vp, _u64, _vp]),
     "mgq_clover_vjp_scratch_bytes": (ctypes.c_uint64, [_P]),
     "mgq_clover_vjp": (_st, [_P, _i, _d, _vp, _vp, _u64, _vp]),

@@ -215,6 +215,24 @@ def mgq_topo_charge(lat: Lattice, stream=None):
     return float(E.value), float(Q.value)
 
 
+def mgq_topo_charge_improved(lat: Lattice, stream=None) -> np.ndarray:
+    """[Q_improved, Q_1x1, Q_2x2, Q_3x3]: the three-loop improved charge and its m x m clover parts."""
+    out = np.zeros(4)
+    call("mgq_topo_charge_improved", lat.ref, ctypes.c_void_p(out.ctypes.data), _stream_handle(stream))
+    return out
+
+
+def mgq_wilson_flow_times(lat: Lattice, t_end: float, eps: float, t_meas, charge: str = "clover", stream=None):
+    """Flow to t_end with steps eps shortened to land on every t_meas; returns E, Q at t_meas.
+    charge: "clover" or "improved" (three-loop improved Q)."""
+    tm = np.ascontiguousarray(np.asarray(t_meas, dtype=np.float64))
+    E, Q = np.zeros(tm.size), np.zeros(tm.size)
+    call("mgq_wilson_flow_times", lat.ref, float(t_end), float(eps), ctypes.c_void_p(tm.ctypes.data), int(tm.size),
+         {"clover": 0, "improved": 1}[charge], ctypes.c_void_p(E.ctypes.data), ctypes.c_void_p(Q.ctypes.data),
+         _stream_handle(stream))
+    return E, Q
+
+
 def mgq_wilson_flow(lat: Lattice, eps: float, n_steps: int, meas_every: int, stream=None):
     m = n_steps // meas_every + 1
     E, Q = np.zeros(m), np.zeros(m)
@@ -366,6 +384,11 @@ def load_checkpoint(path: str, device="cuda"):
 def mgq_flow_vjp(lat: Lattice, psi: torch.Tensor, scale: float, lam: torch.Tensor, stream=None) -> None:
     """lam += scale * DZ(W)^T psi for the flow generator Z(W) = -TA(W A(W)) at the lattice's links."""
     call("mgq_flow_vjp", lat.ref, _ptr(psi), float(scale), _ptr(lam), _stream_handle(stream))
+
+
+def mgq_exp_vjp(lat: Lattice, omega: torch.Tensor, g_in: torch.Tensor, g_out: torch.Tensor, stream=None) -> None:
+    """g_out = J(omega)^T g_in: a cotangent at exp(omega) U pulled back to omega."""
+    call("mgq_exp_vjp", lat.ref, _ptr(omega), _ptr(g_in), _ptr(g_out), _stream_handle(stream))
 
 
 def flow_adjoint_scratch(lat: Lattice) -> torch.Tensor:

@@ -5,10 +5,10 @@ WilsonAction: S(omega) = S_W(exp(omega) U) for an su(3) algebra field omega
 (momentum layout, one 8-vector per link) around the lattice's current links.
 The forward applies the exact exponential (mgq_link_exp_update) to a copy and
 evaluates the Wilson action in FP64 (Sec. III); the backward is the gauge
-force kernel (mgq_hmc_force): dS/domega_a = -F_a, the Lie derivative of S at
-exp(omega) U.  That is the exact gradient at omega = 0 (and the
-left-trivialised gradient elsewhere), which is what HMC and the gradient flow
-use.
+force kernel (mgq_hmc_force), -F_a = the Lie derivative of S at exp(omega) U,
+pulled back to omega through the adjoint differential of the exponential
+(mgq_exp_vjp): dS/domega = J(omega)^T (-F).  At omega = 0, J is the identity
+and the gradient is minus the HMC force.
 """
 from __future__ import annotations
 
@@ -23,7 +23,7 @@ class WilsonAction(torch.autograd.Function):
         moved = api.copy_lattice(lat)
         api.mgq_link_exp_update(moved, omega.detach().contiguous(), 1.0)
         plaq = api.mgq_plaquette(moved)
-        ctx.moved, ctx.beta = moved, float(beta)
+        ctx.moved, ctx.beta, ctx.omega = moved, float(beta), omega.detach().contiguous()
         S = float(beta) * 6.0 * moved.volume * (1.0 - plaq)
         return torch.tensor(S, dtype=torch.float64, device=omega.device)
 
@@ -31,6 +31,7 @@ class WilsonAction(torch.autograd.Function):
     def backward(ctx, grad_S: torch.Tensor):
         F = ctx.moved.new_alg_field()
         api.mgq_hmc_force(ctx.moved, ctx.beta, F)
+        api.mgq_exp_vjp(ctx.moved, ctx.omega, F, F)
         g = (-F.double() * grad_S).to(F.dtype)
         return g, None, None
 
@@ -44,6 +45,9 @@ class FlowedObservable(torch.autograd.Function):
     Sec. IV.B) of exp(omega) U, O one of
       "S": the Wilson action at coupling beta,
       "E": the clover energy density, "Q": the clover topological charge.
+
+    The cotangent at the unflowed field exp(omega) U is pulled back to omega
+    by mgq_exp_vjp, so the gradient is the true omega-derivative.
 
     Forward: the flow kernels, keeping a copy of the field every
     `checkpoint_every` steps (default sqrt(n_steps)).  Backward: the gradient
@@ -73,7 +77,7 @@ class FlowedObservable(torch.autograd.Function):
         else:
             E, Q = api.mgq_topo_charge(W)
             value = E if observable == "E" else Q
-        ctx.W, ctx.ckpts, ctx.k = W, ckpts, k
+        ctx.W, ctx.ckpts, ctx.k, ctx.omega = W, ckpts, k, omega.detach().contiguous()
         ctx.obs, ctx.beta, ctx.eps, ctx.n = observable, float(beta), float(eps), int(n_steps)
         return torch.tensor(value, dtype=torch.float64, device=omega.device)
 
@@ -98,6 +102,7 @@ class FlowedObservable(torch.autograd.Function):
             for w0 in reversed(starts):
                 seg.links.copy_(w0)
                 api.mgq_wilson_flow_step_adjoint(seg, ctx.eps, lam, scratch)
+        api.mgq_exp_vjp(W, ctx.omega, lam, lam)   # from exp(omega) U back to omega
         return (lam.double() * grad_L).to(lam.dtype), None, None, None, None, None, None
 
 

@@ -63,6 +63,32 @@ mgq_status clover_into(const mgq_lattice* lat, double* partials, double* dev_out
     return cuda_check("clover");
 }
 
+mgq_status improved_charge_into(const mgq_lattice* lat, double* partials, double* dev_out, cudaStream_t st);
+
+// One RK3 step of size eps with the workspace's algebra buffer B:
+// Z_i = eps Z(W_i), Z(W) = -TA(W A(W));
+// W1 = exp(Z0/4) W0; W2 = exp(8/9 Z1 - 17/36 Z0) W1; W3 = exp(3/4 Z2 - 8/9 Z1 + 17/36 Z0) W2
+static mgq_status flow_step(mgq_lattice* lat, void* B, double eps, cudaStream_t st) {
+    mgq_status s;
+    if ((s = force_accumulate(lat, B, -eps, 0.0, st))) return s;                       // B = Z0
+    if ((s = exp_update(lat, B, 0.25, st))) return s;
+    if ((s = force_accumulate(lat, B, -eps * 8.0 / 9.0, -17.0 / 36.0, st))) return s;  // B = 8/9 Z1 - 17/36 Z0
+    if ((s = exp_update(lat, B, 1.0, st))) return s;
+    if ((s = force_accumulate(lat, B, -eps * 0.75, -1.0, st))) return s;               // B = 3/4 Z2 - B
+    return exp_update(lat, B, 1.0, st);
+}
+
+// E and Q of the current links into meas[0], meas[1] (device); charge 1 takes
+// the three-loop improved Q (its four values pass through tmp[0..3]).
+static mgq_status measure_EQ(const mgq_lattice* lat, int charge, double* meas, double* tmp, cudaStream_t st) {
+    mgq_status s = clover_into(lat, ws_partials(lat), meas, st);
+    if (s || !charge) return s;
+    if ((s = improved_charge_into(lat, ws_partials(lat), tmp, st))) return s;
+    if (cudaMemcpyAsync(meas + 1, tmp, sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return cuda_check("measure_EQ");
+    return MGQ_OK;
+}
+
 }  // namespace mgq
 
 using namespace mgq;
@@ -100,19 +126,54 @@ mgq_status mgq_wilson_flow(mgq_lattice* lat, double eps, int n_steps, int meas_e
             m++;
         }
         if (k == n_steps) break;
-        // Z_i = eps Z(W_i), Z(W) = -TA(W A(W)):
-        // W1 = exp(Z0/4) W0; W2 = exp(8/9 Z1 - 17/36 Z0) W1; W3 = exp(3/4 Z2 - 8/9 Z1 + 17/36 Z0) W2
-        if ((s = force_accumulate(lat, B, -eps, 0.0, st))) return s;              // B = Z0
-        if ((s = exp_update(lat, B, 0.25, st))) return s;
-        if ((s = force_accumulate(lat, B, -eps * 8.0 / 9.0, -17.0 / 36.0, st))) return s;  // B = 8/9 Z1 - 17/36 Z0
-        if ((s = exp_update(lat, B, 1.0, st))) return s;
-        if ((s = force_accumulate(lat, B, -eps * 0.75, -1.0, st))) return s;       // B = 3/4 Z2 - B
-        if ((s = exp_update(lat, B, 1.0, st))) return s;
+        if ((s = flow_step(lat, B, eps, st))) return s;
     }
     // gather strided E, Q pairs
     for (int i = 0; i < nm; i++) {
         if (E_out && (s = deliver(meas + 2 * i, E_out + i, 1, st, "mgq_wilson_flow"))) return s;
         if (Q_out && (s = deliver(meas + 2 * i + 1, Q_out + i, 1, st, "mgq_wilson_flow"))) return s;
+    }
+    return MGQ_OK;
+}
+
+mgq_status mgq_wilson_flow_times(mgq_lattice* lat, double t_end, double eps, const double* t_meas, int n_meas,
+                                 int charge, double* E_out, double* Q_out, void* stream) {
+    Trace trace("mgq_wilson_flow_times");
+    mgq_status s = check_lattice(lat, true, "mgq_wilson_flow_times");
+    if (s) return s;
+    if (!(eps > 0.0) || !(t_end >= 0.0) || n_meas < 0 || (n_meas > 0 && !t_meas) || charge < 0 || charge > 1)
+        return fail(MGQ_EINVAL, "mgq_wilson_flow_times: need eps > 0, t_end >= 0, n_meas >= 0, t_meas, charge 0 or 1");
+    if (2 * n_meas + 64 > (int)WS_NSCALARS)
+        return fail(MGQ_EINVAL, "mgq_wilson_flow_times: at most %d measurements", (int)(WS_NSCALARS - 64) / 2);
+    for (int i = 0; i < n_meas; i++)
+        if (!(t_meas[i] >= 0.0) || t_meas[i] > t_end || (i > 0 && t_meas[i] < t_meas[i - 1]))
+            return fail(MGQ_EINVAL, "mgq_wilson_flow_times: t_meas must be ascending within [0, t_end]");
+    if (t_end / eps > 1e8) return fail(MGQ_EINVAL, "mgq_wilson_flow_times: more than 1e8 steps");
+    cudaStream_t st = as_stream(stream);
+    double* sc = ws_scalars(lat);
+    double* meas = sc + 64;  // E at meas[2i], Q at meas[2i+1]
+    void* B = ws_alg(lat);
+    const double tiny = 1e-12 * (t_end > 1.0 ? t_end : 1.0);
+    double t = 0.0;
+    int i = 0;
+    while (i < n_meas && t_meas[i] <= t + tiny) {
+        if ((s = measure_EQ(lat, charge, meas + 2 * i, sc + 24, st))) return s;
+        i++;
+    }
+    while (t < t_end - tiny) {
+        // the next stop: the next measurement time below t_end, else t_end
+        const double stop = (i < n_meas && t_meas[i] < t_end) ? t_meas[i] : t_end;
+        const double h = stop - t < eps ? stop - t : eps;
+        if ((s = flow_step(lat, B, h, st))) return s;
+        t = h == stop - t ? stop : t + h;
+        while (i < n_meas && t_meas[i] <= t + tiny) {
+            if ((s = measure_EQ(lat, charge, meas + 2 * i, sc + 24, st))) return s;
+            i++;
+        }
+    }
+    for (int k = 0; k < n_meas; k++) {
+        if (E_out && (s = deliver(meas + 2 * k, E_out + k, 1, st, "mgq_wilson_flow_times"))) return s;
+        if (Q_out && (s = deliver(meas + 2 * k + 1, Q_out + k, 1, st, "mgq_wilson_flow_times"))) return s;
     }
     return MGQ_OK;
 }

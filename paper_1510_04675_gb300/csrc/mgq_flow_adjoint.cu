@@ -85,6 +85,42 @@ __global__ void __launch_bounds__(128) k_dexp_adjoint(Geom g, Alg<T> Z0, Alg<T> 
     Lam.store(mu, par, h, ln);
 }
 
+// Per link: Gout = J(Om)* Gin = sum_n (-ad_Om)^n Gin / (n+1)!, the pull-back of a
+// cotangent at exp(Om) U to the algebra variable Om.  The series runs until a
+// term drops below the precision's rounding of the partial sum (at most 40
+// terms), so it stays exact for |Om| of order one.  Gin and Gout may alias.
+template <class T>
+__global__ void __launch_bounds__(128) k_exp_vjp(Geom g, Alg<T> Om, Alg<T> Gin, Alg<T> Gout) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 8 * g.Vh) return;
+    const int mp = idx / g.Vh, h = idx - mp * g.Vh, mu = mp >> 1, par = mp & 1;
+    T x[8], l[8];
+    Om.load(mu, par, h, x);
+    Gin.load(mu, par, h, l);
+    const M3<T> X = alg_matrix(x);
+    M3<T> term = alg_matrix(l), sum = term;
+    const T tiny = sizeof(T) == 4 ? T(3e-8) : T(5e-17);
+#pragma unroll 1
+    for (int n = 1; n <= 40; n++) {
+        term = commutator(X, term);
+        const T f = T(-1) / T(n + 1);
+        T tmax = 0, smax = 0;
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                term.e[i][j] = scale(term.e[i][j], f);
+                sum.e[i][j] = sum.e[i][j] + term.e[i][j];
+                tmax = fmax(tmax, fmax(fabs(term.e[i][j].re), fabs(term.e[i][j].im)));
+                smax = fmax(smax, fmax(fabs(sum.e[i][j].re), fabs(sum.e[i][j].im)));
+            }
+        if (tmax <= tiny * smax) break;
+    }
+    T out[8];
+    ta_coeffs(sum, out);
+    Gout.store(mu, par, h, out);
+}
+
 // P <- a0 X0 + a1 X1 + a2 X2 (algebra coefficients, elementwise)
 template <class T>
 __global__ void k_alg_combine(Geom g, Alg<T> P, Alg<T> X0, Alg<T> X1, Alg<T> X2, T a0, T a1, T a2) {
@@ -317,6 +353,27 @@ mgq_status mgq_wilson_flow_step_adjoint(const mgq_lattice* lat, double eps, void
     if ((s = combine(lat, Psi, Xi[0], Xi[1], Xi[2], 0.25, -17.0 / 36.0, 17.0 / 36.0, st))) return s;
     if ((s = flow_vjp(lat, lat->links, Psi, eps, lambda, st))) return s;
     return MGQ_OK;
+}
+
+mgq_status mgq_exp_vjp(const mgq_lattice* lat, const void* omega, const void* g_in, void* g_out, void* stream) {
+    Trace trace("mgq_exp_vjp");
+    mgq_status s = check_lattice(lat, false, "mgq_exp_vjp");
+    if (s) return s;
+    if (!omega || !g_in || !g_out || ((uintptr_t)omega & 15) || ((uintptr_t)g_in & 15) || ((uintptr_t)g_out & 15))
+        return fail(MGQ_EINVAL, "mgq_exp_vjp: omega/g_in/g_out NULL or misaligned");
+    cudaStream_t st = as_stream(stream);
+    const Geom g = make_geom(lat->dims);
+    void* om = const_cast<void*>(omega);
+    void* gi = const_cast<void*>(g_in);
+    if (lat->prec == MGQ_F64)
+        k_exp_vjp<double><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(g, alg_at<double>(om, lat->dims),
+                                                               alg_at<double>(gi, lat->dims),
+                                                               alg_at<double>(g_out, lat->dims));
+    else
+        k_exp_vjp<float><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(g, alg_at<float>(om, lat->dims),
+                                                              alg_at<float>(gi, lat->dims),
+                                                              alg_at<float>(g_out, lat->dims));
+    return cuda_check("mgq_exp_vjp");
 }
 
 }  // extern "C"

@@ -35,10 +35,10 @@ def test_action_gradient_finite_differences(gpu, orc):
         assert abs(fd - ad) < 1e-7 * max(1.0, abs(ad)), (fd, ad)
 
 
-def test_action_gradient_small_omega(gpu, orc):
-    """Away from omega = 0 the backward is the left-trivialised gradient: it
-    differs from d/domega by O(|omega|)."""
-    dims, beta, h = [4, 4, 2, 2], 6.0, 1e-5
+def test_action_gradient_away_from_zero(gpu, orc):
+    """At omega != 0 the backward is the true derivative d/domega S(exp(omega) U):
+    it matches central differences (Richardson, h = 1e-4) for |omega| up to O(1)."""
+    dims, beta, h = [4, 4, 2, 2], 6.0, 1e-4
     lat = gpu.Lattice(dims, "f64", seed=3)
     gpu.mgq_init_links(lat, 1)
     gen = torch.Generator(device="cuda").manual_seed(1)
@@ -46,10 +46,14 @@ def test_action_gradient_small_omega(gpu, orc):
     gpu.zero_alg_padding(lat, base)
     v = torch.randn(base.shape, dtype=torch.float64, device="cuda", generator=gen)
     gpu.zero_alg_padding(lat, v)
-    errs = []
-    for scale in (1e-2, 1e-3):
+    for scale in (1e-2, 0.3, 1.0):
         omega = (scale * base).requires_grad_(True)
         (g,) = torch.autograd.grad(wilson_action(omega, lat, beta), omega)
-        fd = (wilson_action(omega.detach() + h * v, lat, beta) - wilson_action(omega.detach() - h * v, lat, beta)).item() / (2 * h)
-        errs.append(abs(fd - torch.dot(g, v).item()))
-    assert errs[1] < errs[0] / 5   # shrinks linearly with |omega|
+        w0 = omega.detach()
+
+        def cd(e):
+            return (wilson_action(w0 + e * v, lat, beta) - wilson_action(w0 - e * v, lat, beta)).item() / (2 * e)
+
+        fd = (4 * cd(h / 2) - cd(h)) / 3
+        ad = torch.dot(g, v).item()
+        assert abs(fd - ad) < 1e-7 * max(1.0, abs(ad)), (scale, fd, ad)

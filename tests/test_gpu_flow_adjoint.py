@@ -123,3 +123,22 @@ def test_flowed_clover_gradient(gpu, obs):
     fd = (flowed_observable(h * v, lat, obs, eps, n).item() - flowed_observable(-h * v, lat, obs, eps, n).item()) / (2 * h)
     ad = torch.dot(g, v).item()
     assert abs(fd - ad) < 1e-6 * max(1e-3, abs(fd)), (fd, ad)
+
+
+@pytest.mark.parametrize("obs", ["S", "Q"])
+def test_flowed_gradient_away_from_zero(gpu, obs):
+    """At omega != 0 the backward is the true derivative of O(flow(exp(omega) U))."""
+    from paper_1510_04675_gb300.autograd import flowed_observable
+
+    lat = _field(gpu, [4, 4, 4, 4], 41, sweeps=3)
+    eps, n = 0.02, 6
+    gen = torch.Generator(device="cuda").manual_seed(42)
+    w0 = _rand_alg(lat, gen, 0.5)
+    omega = w0.clone().requires_grad_(True)
+    (g,) = torch.autograd.grad(flowed_observable(omega, lat, obs, eps, n, checkpoint_every=2), omega)
+    v = _rand_alg(lat, gen)
+    h = 1e-5
+    fd = (flowed_observable(w0 + h * v, lat, obs, eps, n).item()
+          - flowed_observable(w0 - h * v, lat, obs, eps, n).item()) / (2 * h)
+    ad = torch.dot(g, v).item()
+    assert abs(fd - ad) < 1e-6 * max(1e-3, abs(fd)), (fd, ad)

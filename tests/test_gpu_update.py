@@ -69,9 +69,10 @@ def test_overrelaxation_sweep_parity(gpu, orc, dims):
     lat.from_numpy(U)
     orc.overrelax_sweep(U, dims)
     gpu.mgq_overrelax_sweep(lat)
-    # one sweep: the rounding differences (FMA contraction, summation order) are
-    # amplified by the 1/|w| normalisation of the reflection; tolerance 1e-11
-    assert np.max(np.abs(lat.to_numpy() - U)) < 1e-11
+    # one sweep: within 1e-12 (measured worst 1.3e-13 on hot starts).  Later
+    # sweeps amplify the rounding differences (FMA contraction, summation order)
+    # through the 1/|w| of the reflection, about x20-x100 per sweep.
+    assert np.max(np.abs(lat.to_numpy() - U)) < 1e-12
 
 
 def test_config1_chain_fp64(gpu, orc):

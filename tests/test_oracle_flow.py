@@ -158,3 +158,34 @@ def test_adaptive_controller_rejects_and_lands_on_measurement_times(orc):
     assert ra >= 1 and len(Ea) == len(Eb) == 6
     assert Ea[0] == Eb[0]
     assert np.max(np.abs(Ea - Eb) / Eb) < 1e-5
+
+
+def test_flow_to_measurement_times(orc):
+    """Flow with measurement times (the problem statement's t_meas form): on the
+    step grid it reproduces the fixed-step flow bit for bit; off the grid a step
+    is shortened to land on the time, which keeps the third-order accuracy."""
+    dims = [4, 4, 4, 4]
+    U = orc.init_links(dims, 1, seed=31)
+    orc.update_chain(U, dims, 6.0, 31, 0, 0, 4, 1, 2)
+    W1, W2 = U.copy(), U.copy()
+    E1, Q1 = orc.wilson_flow(W1, dims, 0.02, 10, 5)
+    E2, Q2 = orc.wilson_flow_times(W2, dims, 0.2, 0.02, [0.0, 0.1, 0.2])
+    assert np.array_equal(E1, E2) and np.array_equal(Q1, Q2) and np.array_equal(W1, W2)
+    # off-grid times: t = 0.033 and 0.077 with eps = 0.01, against eps = 0.0005
+    tm = [0.033, 0.077]
+    W3, W4, Wr = U.copy(), U.copy(), U.copy()
+    E3, Q3 = orc.wilson_flow_times(W3, dims, 0.1, 0.01, tm)
+    E4, Q4 = orc.wilson_flow_times(W4, dims, 0.1, 0.005, tm)
+    Er, Qr = orc.wilson_flow_times(Wr, dims, 0.1, 0.0005, tm)
+    assert np.max(np.abs(E3 - Er)) < 1e-6 * np.max(np.abs(Er))
+    ratio = np.max(np.abs(W3 - Wr)) / np.max(np.abs(W4 - Wr))
+    assert 6.0 < ratio < 10.0, ratio  # global error ~ eps^3 with the shortened steps
+    # a single step of the whole length is exactly one flow step
+    W5, W6 = U.copy(), U.copy()
+    orc.wilson_flow_times(W5, dims, 0.037, 1.0, [])
+    orc.flow_step(W6, dims, 0.037)
+    assert np.array_equal(W5, W6)
+    # the improved-charge option measures the improved Q of the flowed field
+    W7 = U.copy()
+    E7, Q7 = orc.wilson_flow_times(W7, dims, 0.05, 0.01, [0.05], charge=1)
+    assert Q7[0] == orc.topo_charge_improved(W7, dims)[0] and E7[0] == orc.clover_EQ(W7, dims)[0]
