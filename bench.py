@@ -38,9 +38,10 @@ METRIC = "link updates/s + force GB/s, 32^4 SU(3), vs plain FP64 GPU; % HBM roof
 UNIT = "link updates/s"
 LINK_BYTES = {"f64": 144, "f32": 72, "f32c12": 48}
 REAL_BYTES = {"f64": 8, "f32": 4, "f32c12": 4}
-# FP32 ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz
-# (a packed FFMA2 issues at half rate, so it does not raise this).  FP64 on this part is far lower.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP32 ALU peak derived from unit counts and clock: SMs (read from the device) x 128 FP32 lanes
+# x 2 flops per FMA x the maximal SM clock (a packed FFMA2 issues at half rate, so it does not
+# raise this).  The measured peak comes from mgq_fma_probe in the same run.  FP64 is far lower.
+FP32_LANES_PER_SM = 128
 # Algorithmic real flops per link (complex multiply 6, complex add 2, 3x3 complex product 198):
 # staple = 12 products + 5 matrix sums = 2466; the force adds U.A (198) and the traceless
 # antihermitian projection and scaled accumulate (36); the overrelaxation adds U.A (198), three
@@ -52,7 +53,7 @@ FLOPS_PER_LINK = {"k_force": 2700, "k_overrelax": 3400, "k_heatbath": 3580}
 def parse_args():
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["mgq", "reference"], default="mgq")
     p.add_argument("--prec", choices=["f64", "f32", "f32c12"], default="f32c12")
@@ -62,7 +63,7 @@ def parse_args():
     p.add_argument("--therm", type=int, default=30, help="untimed thermalisation sweeps before timing")
     p.add_argument("--no-extras", action="store_true", help="skip the FP64/FP32 comparison legs")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--large", action="store_true", help="add the 48^4 FP32/FP64 leg")
+    p.add_argument("--no-large", action="store_true", help="skip the bounded 48^4 FP32/FP64 leg")
     return p.parse_args()
 
 
@@ -137,7 +138,7 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -290,6 +291,32 @@ def ev():
     return torch.cuda.Event(enable_timing=True)
 
 
+def fp32_peaks(api):
+    """FP32 peaks in TFLOP/s: derived from the device's SM count, 128 lanes, 2 flops per
+    FMA and the maximal SM clock; measured with mgq_fma_probe (independent packed FMA
+    chains on every SM, best of 5 launches timed with CUDA events)."""
+    import torch
+
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
+    mhz = float((measured_peaks() or {}).get("sm_max_mhz") or 2070.0)
+    derived = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    api.fma_probe(64, sink)
+    torch.cuda.synchronize()
+    best = 0.0
+    for _ in range(5):
+        a, b = ev(), ev()
+        a.record()
+        flops = api.fma_probe(20000, sink)
+        b.record()
+        torch.cuda.synchronize()
+        best = max(best, flops / (a.elapsed_time(b) * 1e-3) / 1e12)
+    return {"measured_tflops": best, "derived_tflops": derived, "sms": sms, "sm_max_mhz": mhz,
+            "how": "mgq_fma_probe: 4 blocks x 256 threads per SM, 8 independent packed-FMA chains per thread, "
+                   "best of 5 launches (CUDA events); derived = SMs x 128 lanes x 2 x max SM clock"}
+
+
 def time_sweeps(api, lat, beta, n_or, steps, sweep0):
     """Link updates/s of `steps` compound sweeps (device-resident)."""
     import torch
@@ -305,10 +332,27 @@ def time_sweeps(api, lat, beta, n_or, steps, sweep0):
     return (1 + n_or) * 4 * lat.volume * steps / (a.elapsed_time(b) * 1e-3)
 
 
-def batched_leg(api, beta_lo=5.8, beta_hi=6.1, n_sweeps=20, n_or=4, seed=4242):
+def _graph_of(fn):
+    """fn(stream) captured into a CUDA graph after one warm-up run on a side stream."""
+    import torch
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn(s)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn(torch.cuda.current_stream())
+    return g
+
+
+def batched_leg(api, peak_gbs, beta_lo=5.8, beta_hi=6.1, n_sweeps=20, n_or=4, seed=4242):
     """256 fine lattices (96 x 12^4, 96 x 16^4, 64 x 8^3x16, FP32 12-real) prolongated
-    from coarse lattices thermalised at beta in [5.8, 6.1]; n_sweeps compound sweeps
-    of all of them with per-lattice FP64 plaquettes, replayed from one CUDA graph."""
+    from coarse lattices thermalised at beta in [5.8, 6.1] with the paper's 0.001 %
+    stopping rule on the device (mgq_prolongate_batched), then n_sweeps compound
+    sweeps of all of them with per-lattice FP64 plaquettes; prolongation and sweeps
+    replayed from one CUDA graph."""
     import numpy as np
     import torch
 
@@ -320,35 +364,99 @@ def batched_leg(api, beta_lo=5.8, beta_hi=6.1, n_sweeps=20, n_or=4, seed=4242):
         api.mgq_init_links(c, 1)
     api.mgq_update_sweeps_batched(api.Batch(coarse, betas), 0, 30, 1, n_or)
     fine = [api.Lattice(s, "f32c12", seed=seed + 1, lattice_id=i) for i, s in enumerate(shapes)]
-    for c, f in zip(coarse, fine):
-        api.mgq_prolongate(c, f, 0.05, 0.0, 10)  # fixed 10 APE steps per stage
-    del coarse
-    batch = api.Batch(fine, betas, max_sweeps=1)
-    P = batch.plaquette_buffer(1)
-    s = torch.cuda.Stream()
-    s.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(s):
-        for i in range(2):
-            api.mgq_update_sweeps_batched(batch, i, 1, 1, n_or, P, stream=s)
-    torch.cuda.current_stream().wait_stream(s)
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        api.mgq_update_sweeps_batched(batch, 2, 1, 1, n_or, P, stream=torch.cuda.current_stream())
-    g.replay()
+    pb = api.ProlongBatch(coarse, fine)
+    # the stopping rule on the device, the host reading the finished count every 32 iterations
+    _, t_pro = _timed(lambda: api.mgq_prolongate_batched(pb, 0.05, 1e-5, 10000))
+    iters = pb.iters.cpu().numpy()
+    budget = int(iters.sum(axis=1).max()) + 3
+    batch = api.Batch(fine, betas, max_sweeps=n_sweeps)
+    P = batch.plaquette_buffer(n_sweeps)
+
+    def sweeps(st):
+        api.mgq_update_sweeps_batched(batch, 2, n_sweeps, 1, n_or, P, stream=st)
+
+    def pipeline(st):
+        api.mgq_prolongate_batched(pb, 0.05, 1e-5, 10000, iter_budget=budget, stream=st)
+        sweeps(st)
+
+    g_sw, g_all = _graph_of(sweeps), _graph_of(pipeline)
+    g_all.replay()
+    g_sw.replay()
     torch.cuda.synchronize()
-    a, b = ev(), ev()
-    a.record()
-    for _ in range(n_sweeps):
-        g.replay()
-    b.record()
-    torch.cuda.synchronize()
-    sec = a.elapsed_time(b) * 1e-3
+    ms_all, ms_sw = [], []
+    for _ in range(3):
+        a, b, c = ev(), ev(), ev()
+        a.record()
+        g_all.replay()
+        b.record()
+        g_sw.replay()
+        c.record()
+        torch.cuda.synchronize()
+        ms_all.append(a.elapsed_time(b))
+        ms_sw.append(b.elapsed_time(c))
+    ms_all, ms_sw = sorted(ms_all)[1], sorted(ms_sw)[1]
     V = sum(int(np.prod(x)) for x in shapes)
+    sec = ms_sw * 1e-3
+    bytes_per_sweep = 8 * (1 + n_or) * 9 * 48 * (V // 2)   # 9 link transfers per update, 12-real links
+    achieved = bytes_per_sweep * n_sweeps / sec / 1e9
     return {"lattices": len(shapes), "sites": V, "sweeps": n_sweeps,
             "link_updates_per_s": (1 + n_or) * 4 * V * n_sweeps / sec, "ms_per_sweep": 1e3 * sec / n_sweeps,
-            "plaquette_mean": float(P.mean().item()), "graph": True,
-            "workload": "96x12^4 + 96x16^4 + 64x8^3x16, beta in [5.8, 6.1], prolongated (10 APE steps/stage), "
-                        "1 HB + 4 OR per sweep, FP32 12-real, per-lattice FP64 plaquette"}
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                         "frac": achieved / peak_gbs, "traffic": None,
+                         "algorithmic_bytes_per_sweep": bytes_per_sweep,
+                         "note": "all 40 sub-sweep launches of a compound sweep over the 256 lattices"},
+            "prolongation": {"ms_host_polled": 1e3 * t_pro, "ms_in_graph": ms_all - ms_sw,
+                             "iteration_budget": budget, "ape_steps_max": [int(v) for v in iters.max(axis=0)],
+                             "ape_steps_mean": [float(v) for v in iters.mean(axis=0)],
+                             "finished": int(pb.n_done.item())},
+            "ms_graph_prolongation_plus_sweeps": ms_all,
+            "plaquette_mean": float(P[-1].mean().item()), "graph": True,
+            "workload": "96x12^4 + 96x16^4 + 64x8^3x16 prolongated from coarse 6^4, 8^4, 4^3x8 (beta in [5.8, 6.1]) "
+                        "with the 0.001 % stopping rule on the device, 20 x (1 HB + 4 OR), FP32 12-real, "
+                        "per-lattice FP64 plaquette; one CUDA graph"}
+
+
+def multilevel_leg(api, n_sweeps=20, n_or=4):
+    """Two refinement levels 8^4 -> 16^4 -> 32^4 (Sec. I-II), the coarsest lattice
+    thermalised in-run at beta = 5.7, rethermalised at 6.0 and 6.3 (nominal couplings
+    for halving the spacing twice; the paper's RG matching is not part of this), each
+    level's prolongation with the 0.001 % stopping rule on the device; the whole chain
+    (two prolongations, 2 x 20 compound sweeps) replayed from one CUDA graph."""
+    import torch
+
+    c8 = api.Lattice([8] * 4, "f32c12", seed=31)
+    api.mgq_init_links(c8, 1)
+    api.mgq_update_sweeps(c8, 5.7, 0, 100, 1, 4)
+    l16 = api.Lattice([16] * 4, "f32c12", seed=32)
+    l32 = api.Lattice([32] * 4, "f32c12", seed=33)
+    p1, p2 = api.ProlongBatch([c8], [l16]), api.ProlongBatch([l16], [l32])
+    b16, b32 = api.Batch([l16], [6.0], max_sweeps=1), api.Batch([l32], [6.3], max_sweeps=1)
+
+    def chain(st, budgets=(0, 0)):
+        api.mgq_prolongate_batched(p1, 0.05, 1e-5, 10000, iter_budget=budgets[0], stream=st)
+        api.mgq_update_sweeps_batched(b16, 0, n_sweeps, 1, n_or, stream=st)
+        api.mgq_prolongate_batched(p2, 0.05, 1e-5, 10000, iter_budget=budgets[1], stream=st)
+        api.mgq_update_sweeps_batched(b32, 0, n_sweeps, 1, n_or, stream=st)
+
+    _, t_host = _timed(lambda: chain(torch.cuda.current_stream()))
+    budgets = (int(p1.iters.sum().item()) + 3, int(p2.iters.sum().item()) + 3)
+    iters = [p1.iters[0].tolist(), p2.iters[0].tolist()]
+    g = _graph_of(lambda st: chain(st, budgets))
+    g.replay()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(3):
+        a, b = ev(), ev()
+        a.record()
+        g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return {"workload": "8^4 (beta 5.7) -> 16^4 (6.0) -> 32^4 (6.3), prolongation with the 0.001 % rule on the "
+                        f"device, {n_sweeps} x (1 HB + {n_or} OR) per fine level, f32c12, one CUDA graph",
+            "ape_steps": iters, "iteration_budgets": list(budgets), "ms_graph": sorted(ms)[1],
+            "ms_host_polled": 1e3 * t_host, "finished": [int(p1.n_done.item()), int(p2.n_done.item())],
+            "plaquette_16": api.mgq_plaquette(l16), "plaquette_32": api.mgq_plaquette(l32)}
 
 
 def _timed(fn):
@@ -424,40 +532,75 @@ def flow_leg(api, dims=(24, 24, 24, 48), beta=5.96, t0=2.79, prec="f32c12"):
             "t2E_at_t0": float(t0 * t0 * Ea[1])}
 
 
-def large_leg(api, beta=6.2):
-    """48^4 at beta = 6.2, FP32 12-real and FP64 side by side: sweeps, HMC, flow to t = 3."""
-    out = {}
-    for prec, n_sw, n_traj, n_flow in [("f32c12", 100, 10, 300), ("f64", 2, 1, 10)]:
-        lat = api.Lattice([48] * 4, prec, seed=97, with_mom=True)
-        api.mgq_init_links(lat, 1)
-        _, t_sw = _timed(lambda: api.mgq_update_sweeps(lat, beta, 0, n_sw, 1, 1))
-        _, t_h = _timed(lambda: [api.mgq_hmc_trajectory(lat, beta, 1.0, 40, t, 0) for t in range(n_traj)])
-        w = api.copy_lattice(lat)
-        (E, Q), t_f = _timed(lambda: api.mgq_wilson_flow(w, 0.01, n_flow, n_flow))
-        V = 48**4
-        out[prec] = {"sweeps": n_sw, "link_updates_per_s": 2 * 4 * V * n_sw / t_sw,
-                     "ms_per_hmc_trajectory_40_steps": 1e3 * t_h / n_traj, "ms_per_flow_step": 1e3 * t_f / n_flow,
-                     "Q_flowed": float(Q[-1])}
-        del w
-        if prec == "f32c12":
-            # dQ(W_t)/d omega at omega = 0 through the checkpointed adjoint flow (t = 3)
-            import torch
+def large_leg(api, peak_gbs, beta=6.2, n_sweeps=100, n_traj=10, n_flow=100):
+    """48^4 at beta = 6.2, FP32 12-real and FP64 side by side, bounded to stay within the
+    default run: 100 x (1 HB + 1 OR) in FP32 (FP64: 2), 10 HMC trajectories of 40 steps
+    (FP64: 1), Wilson flow eps = 0.01 to t = 1 in FP32 (the workload asks for t = 3; FP64: 10
+    steps) with clover Q, and dQ/d omega of the flowed Q through checkpointed adjoint flow
+    steps.  The FP32-vs-FP64 errors come from the same configuration, the same Philox
+    words and the same momenta in both formats."""
+    import numpy as np
+    import torch
 
-            from paper_1510_04675_gb300.autograd import flowed_observable
+    from paper_1510_04675_gb300.autograd import flowed_observable
 
-            omega = torch.zeros_like(lat.new_alg_field(), requires_grad=True)
+    V = 48**4
+    out = {"reductions": f"FP32: {n_sweeps} sweeps, {n_traj} trajectories, flow to t = {n_flow * 0.01:g}; "
+                         "FP64: 2 sweeps, 1 trajectory, 10 flow steps"}
+    l32 = api.Lattice([48] * 4, "f32c12", seed=97, with_mom=True)
+    api.mgq_init_links(l32, 1)
+    _, t_sw = _timed(lambda: api.mgq_update_sweeps(l32, beta, 0, n_sweeps, 1, 1))
+    r = 2 * 4 * V * n_sweeps / t_sw
+    out["f32c12"] = {"sweeps": n_sweeps, "link_updates_per_s": r, "hbm_gbs": r * 9 * 48 / 1e9,
+                     "hbm_frac": r * 9 * 48 / 1e9 / peak_gbs}
+    # the same configuration in FP64
+    canon = torch.empty(V * 72, dtype=torch.float64, device="cuda")
+    api.mgq_export_links(l32, canon)
+    l64 = api.Lattice([48] * 4, "f64", seed=97, with_mom=True)
+    api.mgq_import_links(l64, canon)
+    del canon
+    start32, start64 = api.copy_lattice(l32), api.copy_lattice(l64)
+    _, t64 = _timed(lambda: api.mgq_update_sweeps(l64, beta, n_sweeps, 2, 1, 1))
+    out["f64"] = {"sweeps": 2, "link_updates_per_s": 2 * 4 * V * 2 / t64}
+    # one compound sweep from the same start with the same random words
+    p32 = api.mgq_update_sweeps(l32, beta, n_sweeps, 1, 1, 1, plaq_out=True)[0]
+    s64 = api.copy_lattice(start64)
+    p64 = api.mgq_update_sweeps(s64, beta, n_sweeps, 1, 1, 1, plaq_out=True)[0]
+    del s64
+    # HMC: trajectories of 40 steps; trajectory 0 in both formats from the same start
+    l32.links.copy_(start32.links)
+    l64.links.copy_(start64.links)
+    d32, _ = api.mgq_hmc_trajectory(l32, beta, 1.0, 40, 0, 0)
+    (d64, _), t_h64 = _timed(lambda: api.mgq_hmc_trajectory(l64, beta, 1.0, 40, 0, 0))
+    _, t_h = _timed(lambda: [api.mgq_hmc_trajectory(l32, beta, 1.0, 40, t, 0) for t in range(1, n_traj + 1)])
+    out["f32c12"]["ms_per_hmc_trajectory_40_steps"] = 1e3 * t_h / n_traj
+    out["f64"]["ms_per_hmc_trajectory_40_steps"] = 1e3 * t_h64
+    # flow from the common start
+    w32, w64 = api.copy_lattice(start32), api.copy_lattice(start64)
+    (E32, Q32), t_f = _timed(lambda: api.mgq_wilson_flow(w32, 0.01, n_flow, 10))
+    (E64, Q64), t_f64 = _timed(lambda: api.mgq_wilson_flow(w64, 0.01, 10, 10))
+    out["f32c12"]["ms_per_flow_step"] = 1e3 * t_f / n_flow
+    out["f32c12"]["Q_flowed"] = float(Q32[-1])
+    out["f64"]["ms_per_flow_step"] = 1e3 * t_f64 / 10
+    out["fp32_vs_fp64"] = {"plaquette_rel_after_one_sweep": abs(p32 - p64) / abs(p64),
+                           "hmc_dH_abs": abs(d32 - d64), "dH_f64": d64,
+                           "flow_E_rel_t0.1": abs(E32[1] - E64[1]) / abs(E64[1]), "flow_Q_abs_t0.1": abs(Q32[1] - Q64[1])}
+    del w32, w64, l64, start64
+    torch.cuda.empty_cache()
+    # dQ(W_t)/d omega at omega = 0 through the checkpointed adjoint flow
+    l32.links.copy_(start32.links)
+    omega = torch.zeros_like(l32.new_alg_field(), requires_grad=True)
 
-            def fwd_bwd():
-                q = flowed_observable(omega, lat, "Q", 0.01, n_flow)
-                q.backward()
-                return q
+    def fwd_bwd():
+        q = flowed_observable(omega, l32, "Q", 0.01, n_flow)
+        q.backward()
+        return q
 
-            q, t_fb = _timed(fwd_bwd)
-            out[prec]["ms_flowed_Q_forward_backward"] = 1e3 * t_fb
-            out[prec]["grad_norm"] = float(omega.grad.norm())
-            out[prec]["Q_flowed_autograd"] = float(q.detach())
-            del omega
-        del lat
+    q, t_fb = _timed(fwd_bwd)
+    out["f32c12"]["ms_flowed_Q_forward_backward"] = 1e3 * t_fb
+    out["f32c12"]["flow_t"] = n_flow * 0.01
+    out["f32c12"]["grad_norm"] = float(omega.grad.norm())
+    del omega, l32, start32
     return out
 
 
@@ -479,6 +622,8 @@ def run_mgq(args, dims, world, rank, local):
     if n_or < 2:
         raise SystemExit("bench.py times plain and plaquette-measuring overrelaxation sweeps: needs --n-or >= 2")
 
+    arm_clk = ClockSampler(torch.cuda.current_device())  # the whole GPU arm, extra legs included
+    arm_clk.start()
     lat = api.Lattice(dims, args.prec, seed=1234, lattice_id=rank, with_mom=True)
     api.mgq_init_links(lat, 1)
     api.mgq_update_sweeps(lat, beta, 0, args.therm, 1, n_or)
@@ -548,13 +693,17 @@ def run_mgq(args, dims, world, rank, local):
                 "traffic": traffic_from_profiles(name, tag), "kernel": name, "ms_per_launch": ms,
                 "algorithmic_bytes_per_launch": bytes_per_launch, "peak_source": peak_src}
 
+    fp32 = fp32_peaks(api)
+
     def alu_roof(name, links, ms):
         if args.prec == "f64":
             return None
         ach = FLOPS_PER_LINK[name] * links / (ms * 1e-3) / 1e12
-        return {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None, "kernel": name, "ms_per_launch": ms,
-                "algorithmic_flops_per_link": FLOPS_PER_LINK[name], "peak_source": "derived (unit counts x clock)"}
+        return {"bound": "alu", "achieved": ach, "peak": fp32["measured_tflops"], "unit": "TFLOP/s",
+                "frac": ach / fp32["measured_tflops"], "peak_derived": fp32["derived_tflops"],
+                "frac_derived": ach / fp32["derived_tflops"], "traffic": None, "kernel": name, "ms_per_launch": ms,
+                "algorithmic_flops_per_link": FLOPS_PER_LINK[name],
+                "peak_source": "measured FP32 FMA peak (mgq_fma_probe, same run)"}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -569,29 +718,75 @@ def run_mgq(args, dims, world, rank, local):
         "ms_overrelax_sweep_with_plaquette": last_ms,
         "clocks": clocks,
     }
+    if clocks and clocks.get("sm_mhz"):
+        # clock-normalised step: SM cycles per step at the median clock of the timed region
+        out["mcycles_per_step"] = 1e3 * t / K * clocks["sm_mhz"] * 1e-3
 
-    # HMC force + momentum update (algorithmic GB/s: links once + P read and written)
+    out["fp32_peak"] = fp32
+
+    # HMC gauge force.  The leapfrog's P-step (force fused with P <- P + eps F: every link
+    # read once, P read and written) is the kernel the trajectory runs; the standalone
+    # force (P written only) is reported beside it.  Both are ALU-bound on this part:
+    # about 2700 flops per link against 112 (80) bytes is above the FP32 ridge, so the
+    # HBM fraction is context and the ALU fraction against the measured peak is the bar.
     try:
         F = lat.new_alg_field()
-        for _ in range(3):
-            api.mgq_hmc_force(lat, beta, F)
-        torch.cuda.synchronize()
-        a, b = ev(), ev()
         nf = 20
-        a.record()
-        for _ in range(nf):
-            api.mgq_hmc_force(lat, beta, F)
-        b.record()
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / nf
-        fb = 4 * V * (lb + 8 * REAL_BYTES[args.prec])
-        out["force_gbs"] = fb / (ms * 1e-3) / 1e9
-        out["force_ms"] = ms
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            a, b = ev(), ev()
+            a.record()
+            for _ in range(nf):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / nf
+
+        ms_step = timed(lambda: api.mgq_hmc_momentum_step(lat, beta, 1e-30))
+        ms_force = timed(lambda: api.mgq_hmc_force(lat, beta, F))
+        rb = REAL_BYTES[args.prec]
+        b_step, b_force = 4 * V * (lb + 16 * rb), 4 * V * (lb + 8 * rb)
+        out["force_step"] = {"kernel": "k_force (P <- P + eps F)", "ms_per_launch": ms_step,
+                             "algorithmic_bytes_per_launch": b_step, "bytes_per_link": lb + 16 * rb,
+                             "hbm_gbs": b_step / (ms_step * 1e-3) / 1e9,
+                             "hbm_frac": b_step / (ms_step * 1e-3) / 1e9 / peak,
+                             "roofline": alu_roof("k_force", 4 * V, ms_step)}
+        out["force_gbs"] = b_force / (ms_force * 1e-3) / 1e9
+        out["force_ms"] = ms_force
         out["force_roofline_frac"] = out["force_gbs"] / peak
-        out["force_roofline"] = alu_roof("k_force", 4 * V, ms)
+        out["force_roofline"] = alu_roof("k_force", 4 * V, ms_force)
     except Exception as e:  # noqa: BLE001 - reported, not hidden
         out["force_gbs"] = None
         out["force_error"] = str(e)[:200]
+
+    # The reunitarisation projection in FP32 (what the update kernels run) against an FP64
+    # projection of the same FP32 links: time per pass over all 4V links, unitarity after it.
+    if args.prec != "f64":
+        try:
+            w = api.copy_lattice(lat)
+            res = {}
+            for key, f64 in (("fp32_projection", False), ("fp64_projection", True)):
+                api.mgq_reunitarize(w, f64)
+                torch.cuda.synchronize()
+                a, b = ev(), ev()
+                a.record()
+                for _ in range(10):
+                    api.mgq_reunitarize(w, f64)
+                b.record()
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b) / 10
+                res[key] = {"ms_per_pass": ms, "ns_per_link": 1e6 * ms / (4 * V),
+                            "unitarity_violation": api.mgq_check_unitarity(w)}
+            extra = (res["fp64_projection"]["ns_per_link"] - res["fp32_projection"]["ns_per_link"]) * (V // 2) * 1e-3
+            res["extra_us_per_subsweep_if_fp64"] = extra
+            res["heatbath_us_per_subsweep"] = 1e3 * hb_ms
+            out["reunitarisation"] = res
+            del w
+        except Exception as e:  # noqa: BLE001 - reported in the line
+            out["reunitarisation"] = {"error": str(e)[:200]}
 
     # End to end through the C ABI: every step uploads its input links from pinned
     # host memory and reads its plaquette back to pinned host memory.  Two device
@@ -644,16 +839,17 @@ def run_mgq(args, dims, world, rank, local):
         out["speedup_vs_fp64"] = (value / world) / out["fp64_plain_link_updates_per_s"]
         del lat, host_links
         torch.cuda.empty_cache()
-        legs = [("batched", batched_leg), ("hmc_24", hmc_leg), ("multiscale_16", multiscale_leg),
-                ("flow_24x48", flow_leg)]
-        if args.large:
-            legs.append(("large_48", large_leg))
+        legs = [("batched", lambda a: batched_leg(a, peak)), ("multilevel_8_16_32", multilevel_leg),
+                ("hmc_24", hmc_leg), ("multiscale_16", multiscale_leg), ("flow_24x48", flow_leg)]
+        if not args.no_large:
+            legs.append(("large_48", lambda a: large_leg(a, peak)))
         for name, fn in legs:
             try:
                 out[name] = fn(api)
             except Exception as e:  # noqa: BLE001 - reported in the line
                 out[name] = {"error": str(e)[:200]}
             torch.cuda.empty_cache()
+    out["clocks_gpu_arm"] = arm_clk.stop()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample(dims, beta)
     if rank == 0:

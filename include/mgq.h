@@ -115,11 +115,27 @@ mgq_status mgq_set_block_size(int kernel, int prec, int threads);
 /* Current value, 0 for an unknown kernel or precision. */
 int mgq_get_block_size(int kernel, int prec);
 
+/* FP32 arithmetic probe: one launch of independent packed FP32 FMA chains on
+ * every SM (4 blocks of 256 threads per SM, `iters` iterations of 16 packed
+ * FMAs per thread); *sink (device, 4 bytes) receives a value that depends on
+ * every chain.  Returns the number of floating-point operations the launch
+ * performs (2 per FMA), 0 on a bad argument; time it with events on `stream`
+ * to measure the FP32 peak that the ALU-bound kernels are compared with. */
+uint64_t mgq_fma_probe(int iters, float* sink, void* stream);
+
 /* ---- fields ---------------------------------------------------------------- */
 /* Start configurations (Sec. IV.E): start = 0 cold (unit links, the ordered
  * delta-function start), start = 1 hot (Haar-random SU(3) per link from the
  * hot-start Philox stream).  Errors: MGQ_EINVAL. */
 mgq_status mgq_init_links(mgq_lattice* lat, int start, void* stream);
+
+/* Project every link back onto SU(3) with the Gram-Schmidt reunitarisation the
+ * update kernels apply after each link update (rows 0, 1 normalised and
+ * orthogonalised, row 2 = conj(row0 x row1); the paper is silent on it).  For
+ * FP32 formats fp64_projection = 1 runs the projection in FP64 and rounds the
+ * result to FP32, 0 runs it in FP32; FP64 fields ignore the flag.
+ * Errors: MGQ_EINVAL. */
+mgq_status mgq_reunitarize(mgq_lattice* lat, int fp64_projection, void* stream);
 
 /* Copy a field between the canonical FP64 layout (device pointer `canon`,
  * V*4*18 doubles) and the lattice's own layout.  Import rounds to the
@@ -202,9 +218,13 @@ mgq_status mgq_plaquette(const mgq_lattice* lat, double* plaq_out, void* stream)
  * fixed 64 KiB static device array inside libmgq that every GPU loading the
  * library holds until exit.  Limit: V <= 2,096,896 sites (one partial sum per
  * 256 sites, 8191 slots; e.g. 32^4 fits, 48^4 does not); larger lattices get
- * MGQ_EINVAL and should use mgq_plaquette.  The first call on each device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
+ * MGQ_EINVAL and should use mgq_plaquette.  Every call outside stream capture
+ * looks up the array's device address (cudaGetSymbolAddress) with the calling
+ * device current, so a context re-created after cudaDeviceReset is followed;
+ * a call under stream capture reuses the address of the last call outside
+ * capture on that device, so make a first call before any capture (a captured
+ * call with no such address returns MGQ_EINVAL), and none after a device
+ * reset without a call outside capture in between.  All calls share
  * the one array and it keeps the last call's contents (each call rewrites
  * every slot it reads), so calls that overlap on the GPU -- concurrent
  * streams, or other host threads on the same device -- race and must be
@@ -342,6 +362,12 @@ mgq_status mgq_clover_vjp(const mgq_lattice* lat, int observable, double scale, 
  * (device, mom layout and precision); dP/dt = F for H = sum p^2/2 + S. */
 mgq_status mgq_hmc_force(const mgq_lattice* lat, double beta, void* force_out, void* stream);
 
+/* The P-step of the leapfrog (Sec. IV.D), force fused with the update:
+ * P_mu(x) <- P_mu(x) + eps F(x,mu) on lat->mom, F as in mgq_hmc_force -- the
+ * kernel the trajectory runs (eps = e/2 or e).  One pass reads every link and
+ * reads and writes P.  Errors: MGQ_EINVAL (mom NULL or misaligned, beta <= 0). */
+mgq_status mgq_hmc_momentum_step(mgq_lattice* lat, double beta, double eps, void* stream);
+
 /* The Q-step of the leapfrog (Sec. IV.D): U_mu(x) <- exp(s P_mu(x)) U_mu(x)
  * on every link, P = sum_a p_a X_a read from `alg` (device, mom layout and
  * precision), exact SU(3) exponential (Cayley-Hamilton form of Morningstar
@@ -368,11 +394,38 @@ mgq_status mgq_hmc_trajectory(mgq_lattice* lat, double beta, double tau, int n_s
  * = 0 and 1 elsewhere; then for d = 0, 1, 2 Jacobi APE steps
  * U <- P_SU(3)[U + c sum_{nu: n_nu odd} (T+ + T-)] on the bonds with
  * chi_mu(n) = d + 1 until |S_d(k) - S_d(k-1)| <= rel_tol |S_d(k-1)| or
- * max_iter steps (rel_tol <= 0: exactly max_iter steps).  iters_out (host,
- * 3 ints) and sd_out (host, 3 doubles, optional) receive the steps taken and
- * the final S_d / beta.  Uses fine->work.  Errors: MGQ_EINVAL, MGQ_ENOMEM. */
+ * max_iter steps (rel_tol <= 0: exactly max_iter steps).  The stopping rule
+ * and the stage changes run on the device (Sec. IV.C's 0.001 % rule is
+ * rel_tol = 1e-5); the host reads a finished flag every 32 APE iterations.
+ * iters_out (3 ints) and sd_out (3 doubles), host or device, NULL to skip,
+ * receive the steps taken and the final S_d / beta.  Uses fine->work.
+ * Errors: MGQ_EINVAL, MGQ_ENOMEM. */
 mgq_status mgq_prolongate(const mgq_lattice* coarse, mgq_lattice* fine, double c, double rel_tol,
                           int max_iter, int* iters_out, double* sd_out, void* stream);
+
+/* Bytes of the work buffer of mgq_prolongate_batched for these fine lattices:
+ * the per-lattice stage state and partial sums, and one scratch link field per
+ * lattice; 0 on invalid extents or precision. */
+uint64_t mgq_prolongate_batched_workspace_bytes(const mgq_lattice* fine, int n);
+
+/* Prolongation (as mgq_prolongate) of n independent lattices of possibly
+ * different extents at once -- the N_s configurations refined in parallel
+ * (Sec. II) -- each with its own stage, step count and stopping decision on
+ * the device.  Every APE iteration is two launches over all lattices; a stage
+ * of k steps takes k + 1 iterations, so a lattice whose stages take k0, k1, k2
+ * steps is finished after k0 + k1 + k2 + 3 iterations, and later iterations
+ * leave it alone.  iter_budget = 0: iterate until every lattice finished (the
+ * host reads the finished count every 32 iterations).  iter_budget > 0: run
+ * exactly that many iterations and never synchronise, so the call can be
+ * captured into a CUDA graph; lattices not finished by then keep their newest
+ * field and report the steps of their current stage.  iters_out (3n ints),
+ * sd_out (3n doubles) and n_done_out (the number of finished lattices, 1 int):
+ * host or device, NULL to skip (a host pointer synchronises the stream).
+ * work: device, 256-byte aligned, >= mgq_prolongate_batched_workspace_bytes.
+ * Errors: MGQ_EINVAL, MGQ_ENOMEM. */
+mgq_status mgq_prolongate_batched(const mgq_lattice* coarse, mgq_lattice* fine, int n, double c, double rel_tol,
+                                  int max_iter, int iter_budget, int* iters_out, double* sd_out, int* n_done_out,
+                                  void* work, uint64_t work_bytes, void* stream);
 
 /* Restriction U^c_mu(n/2) = U^f_mu(n) U^f_mu(n + e_mu) at chi(n) = 0. */
 mgq_status mgq_restrict(const mgq_lattice* fine, mgq_lattice* coarse, void* stream);

@@ -71,6 +71,8 @@ SIGNATURES = {
     "mgq_flow_adaptive_scratch_bytes": (ctypes.c_uint64, [_P]),
     "mgq_flow_adaptive_measurements": (ctypes.c_int, [_d, _d]),
     "mgq_hmc_force": (_st, [_P, _d, _vp, _vp]),
+    "mgq_hmc_momentum_step": (_st, [_P, _d, _d, _vp]),
+    "mgq_fma_probe": (ctypes.c_uint64, [_i, _vp, _vp]),
     "mgq_link_exp_update": (_st, [_P, _vp, _d, _vp]),
     "mgq_flow_adjoint_scratch_bytes": (ctypes.c_uint64, [_P]),
     "mgq_flow_vjp": (_st, [_P, _vp, _d, _vp, _vp]),
@@ -80,8 +82,11 @@ SIGNATURES = {
     "mgq_clover_vjp": (_st, [_P, _i, _d, _vp, _vp, _u64, _vp]),
     "mgq_hmc_trajectory": (_st, [_P, _d, _d, _i, _u64, _i, _vp, _vp, _vp]),
     "mgq_prolongate": (_st, [_P, _P, _d, _d, _i, _vp, _vp, _vp]),
+    "mgq_prolongate_batched_workspace_bytes": (ctypes.c_uint64, [_P, _i]),
+    "mgq_prolongate_batched": (_st, [_P, _P, _i, _d, _d, _i, _i, _vp, _vp, _vp, _vp, _u64, _vp]),
     "mgq_restrict": (_st, [_P, _P, _vp]),
     "mgq_check_unitarity": (_st, [_P, _d, _vp, _vp]),
+    "mgq_reunitarize": (_st, [_P, _i, _vp]),
     "mgq_batch_workspace_bytes": (ctypes.c_uint64, [_P, _i, _i]),
     "mgq_set_block_size": (_st, [_i, _i, _i]),
     "mgq_get_block_size": (ctypes.c_int, [_i, _i]),

@@ -281,8 +281,47 @@ def mgq_prolongate(coarse: Lattice, fine: Lattice, c: float = 0.05, rel_tol: flo
     return [int(v) for v in iters], [float(v) for v in sd]
 
 
+class ProlongBatch:
+    """Lattice pairs (coarse -> fine) prolongated together by mgq_prolongate_batched.
+
+    The descriptor arrays, the work buffer and the device result buffers are
+    built once, so repeated calls (and CUDA-graph capture) pass the same pointers.
+    """
+
+    def __init__(self, coarse: Sequence[Lattice], fine: Sequence[Lattice]):
+        if len(coarse) != len(fine) or not fine:
+            raise ValueError("need one fine lattice per coarse lattice")
+        self.coarse, self.fine = list(coarse), list(fine)
+        self.n = len(self.fine)
+        self.carr = (MgqLattice * self.n)(*[l.c for l in self.coarse])
+        self.farr = (MgqLattice * self.n)(*[l.c for l in self.fine])
+        nb = int(_lib.load().mgq_prolongate_batched_workspace_bytes(self.farr, self.n))
+        if nb == 0:
+            raise MgqError(_lib.MGQ_EINVAL, "invalid lattice extents in prolongation batch")
+        dev = self.fine[0].device
+        self.work = torch.zeros(nb, dtype=torch.uint8, device=dev)
+        self.iters = torch.zeros((self.n, 3), dtype=torch.int32, device=dev)
+        self.sd = torch.zeros((self.n, 3), dtype=torch.float64, device=dev)
+        self.n_done = torch.zeros(1, dtype=torch.int32, device=dev)
+
+
+def mgq_prolongate_batched(batch: ProlongBatch, c: float = 0.05, rel_tol: float = 1e-5, max_iter: int = 10000,
+                           iter_budget: int = 0, stream=None) -> None:
+    """Prolongate every pair of the batch; results land in batch.iters, batch.sd
+    (device, per lattice) and batch.n_done.  iter_budget > 0: exactly that many
+    APE iterations, no host synchronisation (graph-capturable)."""
+    call("mgq_prolongate_batched", batch.carr, batch.farr, batch.n, float(c), float(rel_tol), int(max_iter),
+         int(iter_budget), _ptr(batch.iters), _ptr(batch.sd), _ptr(batch.n_done), _ptr(batch.work),
+         int(batch.work.numel()), _stream_handle(stream))
+
+
 def mgq_restrict(fine: Lattice, coarse: Lattice, stream=None) -> None:
     call("mgq_restrict", fine.ref, coarse.ref, _stream_handle(stream))
+
+
+def mgq_reunitarize(lat: Lattice, fp64_projection: bool = False, stream=None) -> None:
+    """Gram-Schmidt projection of every link onto SU(3) (FP32 formats: in FP32 or FP64)."""
+    call("mgq_reunitarize", lat.ref, int(bool(fp64_projection)), _stream_handle(stream))
 
 
 def mgq_check_unitarity(lat: Lattice, tol: float = 0.0, stream=None) -> float:
@@ -326,6 +365,16 @@ def mgq_update_sweeps_batched(batch: Batch, sweep0: int, n_sweeps: int, n_hb: in
          int(n_or), _ptr(plaq_out), _ptr(batch.work), int(batch.work.numel()), _stream_handle(stream))
 
 
+def mgq_hmc_momentum_step(lat: Lattice, beta: float, eps: float, stream=None) -> None:
+    """P <- P + eps F(U) on lat.mom: the leapfrog's fused force + P-step."""
+    call("mgq_hmc_momentum_step", lat.ref, float(beta), float(eps), _stream_handle(stream))
+
+
+def fma_probe(iters: int, sink: torch.Tensor, stream=None) -> int:
+    """Launch the FP32 FMA probe; returns the launch's floating-point operations."""
+    return int(_lib.load().mgq_fma_probe(int(iters), _ptr(sink), _stream_handle(stream)))
+
+
 def mgq_link_exp_update(lat: Lattice, alg: torch.Tensor, s: float = 1.0, stream=None) -> None:
     """U <- exp(s P) U on every link, P from an algebra field in the momentum layout."""
     call("mgq_link_exp_update", lat.ref, _ptr(alg), float(s), _stream_handle(stream))
@@ -339,7 +388,7 @@ def copy_lattice(lat: Lattice, with_mom: bool = False) -> Lattice:
 
 
 # ------------------------------------------------------------------ checkpoints
-_MAGIC = b"MGQCKPT2"  # 2: links in 32-site blocks of planes
+_MAGIC = b"MGQCKPT3"  # 3: links in 32-site blocks of planes, FP32 12-real as 16-byte plane pairs
 
 
 def save_checkpoint(lat: Lattice, path: str, beta: float, sweep: int) -> None:

@@ -366,42 +366,76 @@ __device__ __forceinline__ Cx<float> ldg_cx(const Cx<float>* p) {
 // 6 (rows 0 and 1; row 2 rebuilt on load).  A warp reading one plane of 32
 // consecutive sites reads 256 contiguous bytes, and the planes of one link sit
 // at fixed 256-byte (FP32) steps, so a link costs one address computation.
+// FP32 12-real links pair the planes instead: a block holds the pair-planes
+// (0,1), (2,3), (4,5), each 32 sites x 16 bytes (re, im of plane 2p, then of
+// plane 2p+1), i.e. links[mu][parity][h/32][pair][h%32][4 floats]: a link is
+// three 16-byte loads, a warp's pair-plane 512 contiguous bytes.
 template <class T, int NP>
 struct Links {
     Cx<T>* p;
     int S;  // sites per (mu, parity), a multiple of 64
+    static constexpr bool kPaired = sizeof(T) == 4 && NP == 6;
 
-    __device__ __forceinline__ Cx<T>* base(int mu, int par, int h) const {
-        return p + ((size_t)((mu * 2 + par) * (S >> 5) + (h >> 5)) * NP << 5) + (h & 31);
+    // first element of the 32-site block holding h
+    __device__ __forceinline__ Cx<T>* block(int mu, int par, int h) const {
+        return p + ((size_t)((mu * 2 + par) * (S >> 5) + (h >> 5)) * NP << 5);
+    }
+    __device__ __forceinline__ Cx<T>* base(int mu, int par, int h) const { return block(mu, par, h) + (h & 31); }
+    // the six planes of a paired link: three 16-byte loads
+    __device__ __forceinline__ void load_pairs(int mu, int par, int h, M3<T>& m) const {
+        const float4* q = reinterpret_cast<const float4*>(block(mu, par, h)) + (h & 31);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float4 v = q[k << 5];
+            m.e[(2 * k) / 3][(2 * k) % 3] = mk(v.x, v.y);
+            m.e[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(v.z, v.w);
+        }
     }
     __device__ __forceinline__ M3<T> load(int mu, int par, int h) const {
-        const Cx<T>* b = base(mu, par, h);
         M3<T> m;
+        if constexpr (kPaired) {
+            load_pairs(mu, par, h, m);
+        } else {
+            const Cx<T>* b = base(mu, par, h);
 #pragma unroll
-        for (int r = 0; r < NP / 3; r++)
+            for (int r = 0; r < NP / 3; r++)
 #pragma unroll
-            for (int c = 0; c < 3; c++) m.e[r][c] = ldg_cx(b + ((r * 3 + c) << 5));
+                for (int c = 0; c < 3; c++) m.e[r][c] = ldg_cx(b + ((r * 3 + c) << 5));
+        }
         if (NP == 6) rebuild_row2(m);
         return m;
     }
     // rows 0 and 1 only (row 2 left unset), for factors whose third row is not read
     __device__ __forceinline__ M3<T> load_rows(int mu, int par, int h) const {
-        const Cx<T>* b = base(mu, par, h);
         M3<T> m;
+        if constexpr (kPaired) {
+            load_pairs(mu, par, h, m);
+        } else {
+            const Cx<T>* b = base(mu, par, h);
 #pragma unroll
-        for (int r = 0; r < 2; r++)
+            for (int r = 0; r < 2; r++)
 #pragma unroll
-            for (int c = 0; c < 3; c++) m.e[r][c] = ldg_cx(b + ((r * 3 + c) << 5));
+                for (int c = 0; c < 3; c++) m.e[r][c] = ldg_cx(b + ((r * 3 + c) << 5));
+        }
         return m;
     }
     // load of a link given its lexicographic site (parity from the site)
     __device__ __forceinline__ M3<T> load_lex(int mu, int lex, int par) const { return load(mu, par, lex >> 1); }
     __device__ __forceinline__ void store(int mu, int par, int h, const M3<T>& m) const {
-        Cx<T>* b = base(mu, par, h);
+        if constexpr (kPaired) {
+            float4* q = reinterpret_cast<float4*>(block(mu, par, h)) + (h & 31);
 #pragma unroll
-        for (int r = 0; r < NP / 3; r++)
+            for (int k = 0; k < 3; k++) {
+                const Cx<T> a = m.e[(2 * k) / 3][(2 * k) % 3], b = m.e[(2 * k + 1) / 3][(2 * k + 1) % 3];
+                q[k << 5] = make_float4(a.re, a.im, b.re, b.im);
+            }
+        } else {
+            Cx<T>* b = base(mu, par, h);
 #pragma unroll
-            for (int c = 0; c < 3; c++) b[(r * 3 + c) << 5] = m.e[r][c];
+            for (int r = 0; r < NP / 3; r++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) b[(r * 3 + c) << 5] = m.e[r][c];
+        }
     }
 };
 

@@ -174,6 +174,16 @@ mgq_status mgq_hmc_force(const mgq_lattice* lat, double beta, void* force_out, v
     return force_accumulate(lat, force_out, -beta / 6.0, 0.0, as_stream(stream));
 }
 
+mgq_status mgq_hmc_momentum_step(mgq_lattice* lat, double beta, double eps, void* stream) {
+    Trace trace("mgq_hmc_momentum_step");
+    mgq_status s = check_lattice(lat, false, "mgq_hmc_momentum_step");
+    if (s) return s;
+    if (!(beta > 0.0)) return fail(MGQ_EINVAL, "mgq_hmc_momentum_step: beta must be > 0");
+    if (!(eps == eps)) return fail(MGQ_EINVAL, "mgq_hmc_momentum_step: eps is NaN");
+    if (!lat->mom || ((uintptr_t)lat->mom & 15)) return fail(MGQ_EINVAL, "mgq_hmc_momentum_step: mom NULL or misaligned");
+    return force_accumulate(lat, lat->mom, -eps * beta / 6.0, 1.0, as_stream(stream));
+}
+
 mgq_status mgq_link_exp_update(mgq_lattice* lat, const void* alg, double s, void* stream) {
     mgq_status st = check_lattice(lat, false, "mgq_link_exp_update");
     if (st) return st;

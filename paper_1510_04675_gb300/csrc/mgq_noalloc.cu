@@ -25,18 +25,26 @@ constexpr long NOALLOC_MAX_SITES = (long)NOALLOC_MAX_PARTIALS * NOALLOC_THREADS;
 
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_PARTIALS + 1];
 
-// Device address of g_noalloc_scratch, looked up once per device.
+// Device address of g_noalloc_scratch per device.  Outside stream capture it
+// is looked up on every call (so a context re-created after cudaDeviceReset is
+// picked up); under capture the address of the last call outside capture on
+// that device is used, because the lookup may load the module, which capture
+// forbids.
 constexpr int NOALLOC_MAX_DEVICES = 64;
 static double* g_scratch_addr[NOALLOC_MAX_DEVICES] = {};
 static std::mutex g_scratch_mutex;
 
-static mgq_status scratch_for_current_device(double** out) {
+static mgq_status scratch_for_current_device(cudaStream_t st, double** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return cuda_check("mgq_plaquette_noalloc: cudaGetDevice");
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
         return fail(MGQ_EUNSUPPORTED, "mgq_plaquette_noalloc: device %d beyond %d", dev, NOALLOC_MAX_DEVICES);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return cuda_check("mgq_plaquette_noalloc: cudaStreamIsCapturing");
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
+    if (cap != cudaStreamCaptureStatusNone && !g_scratch_addr[dev])
+        return fail(MGQ_EINVAL, "mgq_plaquette_noalloc: the first call on a device must come before any stream capture");
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -81,9 +89,9 @@ mgq_status mgq_plaquette_noalloc(const mgq_lattice* lat, double* plaq_out, void*
                     "mgq_plaquette_noalloc: %d sites exceed the %ld-site limit of its fixed scratch "
                     "(use mgq_plaquette with a workspace)",
                     g.V, NOALLOC_MAX_SITES);
-    double* scratch = nullptr;
-    if ((s = scratch_for_current_device(&scratch))) return s;
     cudaStream_t st = as_stream(stream);
+    double* scratch = nullptr;
+    if ((s = scratch_for_current_device(st, &scratch))) return s;
     const int nb = (g.V + NOALLOC_THREADS - 1) / NOALLOC_THREADS;
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
         k_plaquette_noalloc<T, NP><<<nb, NOALLOC_THREADS, 0, st>>>(links_of<T, NP>(lat), g, scratch);

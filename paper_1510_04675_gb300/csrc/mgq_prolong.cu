@@ -41,24 +41,6 @@ __device__ __forceinline__ int odd_count_except(const int x[4], int a, int b) {
     return c;
 }
 
-// Transfer: U^f_mu(n) = U^c_mu(n/2) where every coordinate of n is even,
-// U^f_mu(n + e_mu) = 1 there, and every other fine bond = 1.
-template <class T, int NP>
-__global__ void k_transfer(Links<T, NP> Uc, Geom gc, Links<T, NP> Uf, Geom gf) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= 8 * gf.Vh) return;
-    const int mp = idx / gf.Vh, h = idx - mp * gf.Vh, mu = mp >> 1, par = mp & 1;
-    int x[4];
-    cb_coords(gf, par, h, x);
-    M3<T> u = unit3<T>();
-    if (((x[0] | x[1] | x[2] | x[3]) & 1) == 0) {
-        const int xc[4] = {x[0] >> 1, x[1] >> 1, x[2] >> 1, x[3] >> 1};
-        const int lc = lex_of(gc, xc);
-        u = Uc.load(mu, (xc[0] + xc[1] + xc[2] + xc[3]) & 1, lc >> 1);
-    }
-    Uf.store(mu, par, h, u);
-}
-
 // Restriction: U^c_mu(n/2) = U^f_mu(n) U^f_mu(n + e_mu) at n with all coordinates even.
 template <class T, int NP>
 __global__ void k_restrict(Links<T, NP> Uf, Geom gf, Links<T, NP> Uc, Geom gc) {
@@ -75,18 +57,132 @@ __global__ void k_restrict(Links<T, NP> Uf, Geom gf, Links<T, NP> Uc, Geom gc) {
     Uc.store(mu, par, h, u);
 }
 
-// One Jacobi APE step of stage d: for every bond with chi_mu(n) = d + 1,
-// Unew = P_SU(3)[U + c sum_{nu != mu, n_nu odd} (T+_munu + T-_munu)],
-// T+ = U_nu(n) U_mu(n+nu) U_nu(n+mu)^+, T- = U_nu(n-nu)^+ U_mu(n-nu) U_nu(n-nu+mu);
-// reads Uin, writes only the active bonds of Uout.
+// ======================================================= interpolation stages
+// The stages run as a device-side state machine per lattice, so that neither
+// the stopping rule nor the stage changes need the host: every iteration is
+// two launches over all lattices of a call --
+//   k_ape_pb      one Jacobi APE step of the lattice's current stage (buffer
+//                 cur -> 1 - cur), or, at the start of a stage, the copy of the
+//                 previous stage's bonds into the other buffer;
+//   k_sd_pb       the partial action S_d of the lattice's newest field; the
+//                 last block of a lattice to finish (atomic ticket, no waiting)
+//                 sums the per-block partials in a fixed order and advances the
+//                 lattice's state: stop after the first step with
+//                 |S_d(k) - S_d(k-1)| <= rel_tol |S_d(k-1)| or after max_iter
+//                 steps (rel_tol <= 0: exactly max_iter), then the next stage.
+// A stage of k steps takes k + 1 iterations (one to measure its start field);
+// a finished lattice turns every later launch into a no-op.  Launches carry
+// the lattice table as a kernel parameter; the state lives in the workspace.
+
+struct ProlongCtl {
+    int d;        // current stage 0..2; 3 when finished
+    int phase;    // 0: measure S_d of the stage's start field; 1: stepping
+    int it;       // steps taken in the stage
+    int cur;      // buffer (0: the lattice's links, 1: scratch) holding the newest field
+    int iters[3];
+    int counted;  // 1 once the lattice added itself to the finished count
+    double prev;  // S_d after the previous step (or of the start field)
+    double sd[3];
+};
+static_assert(sizeof(ProlongCtl) == 64, "control block layout");
+
+constexpr int PB_CHUNK = 64;       // lattices per launch (kernel-parameter table)
+constexpr int PB_THREADS = 128;
+constexpr int PB_SD_THREADS = 256;
+constexpr int PB_SD_MAXBLK = 64;   // partial-action blocks per lattice
+
+template <class T>
+struct ProDesc {
+    Cx<T>* buf[2];
+    Cx<T>* coarse;
+    Geom gf, gc;
+};
+
+template <class T>
+struct PBatch {
+    int n;
+    int prefix[PB_CHUNK + 1];   // blocks of the per-bond kernels (8 Vh_f bonds each)
+    int sprefix[PB_CHUNK + 1];  // blocks of the partial-action kernel
+    ProDesc<T> d[PB_CHUNK];
+    ProlongCtl* ctl;            // [n]
+    double* partials;           // [sprefix[n]]
+    unsigned* ticket;           // [n]
+    int* ndone;                 // finished lattices of the whole call
+    T c;
+    double rel_tol;
+    int max_iter;
+};
+
+// link field at p with the site stride of geometry g (device side)
 template <class T, int NP>
-__global__ void __launch_bounds__(128) k_ape(Links<T, NP> Uin, Links<T, NP> Uout, Geom g, int d, T c) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ Links<T, NP> field(Cx<T>* p, const Geom& g) {
+    Links<T, NP> l;
+    l.p = p;
+    l.S = g.S;
+    return l;
+}
+
+__device__ __forceinline__ int find_block(const int* prefix, int n, int b) {
+    int lo = 0, hi = n;  // prefix[lo] <= b < prefix[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= b) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// transfer into both buffers of every lattice, and a fresh state
+template <class T, int NP>
+__global__ void __launch_bounds__(PB_THREADS) k_transfer_pb(const __grid_constant__ PBatch<T> B) {
+    const int l = find_block(B.prefix, B.n, blockIdx.x);
+    const ProDesc<T>& D = B.d[l];
+    const int idx = (blockIdx.x - B.prefix[l]) * PB_THREADS + threadIdx.x;
+    if (idx == 0) {
+        ProlongCtl c = {};
+        B.ctl[l] = c;
+        B.ticket[l] = 0u;
+    }
+    if (idx >= 8 * D.gf.Vh) return;
+    const int mp = idx / D.gf.Vh, h = idx - mp * D.gf.Vh, mu = mp >> 1, par = mp & 1;
+    int x[4];
+    cb_coords(D.gf, par, h, x);
+    M3<T> u = unit3<T>();
+    if (((x[0] | x[1] | x[2] | x[3]) & 1) == 0) {
+        const int xc[4] = {x[0] >> 1, x[1] >> 1, x[2] >> 1, x[3] >> 1};
+        const int lc = lex_of(D.gc, xc);
+        u = field<T, NP>(D.coarse, D.gc).load(mu, (xc[0] + xc[1] + xc[2] + xc[3]) & 1, lc >> 1);
+    }
+    field<T, NP>(D.buf[0], D.gf).store(mu, par, h, u);
+    field<T, NP>(D.buf[1], D.gf).store(mu, par, h, u);
+}
+
+// One iteration's bond work.  Stepping (phase 1): every bond with
+// chi_mu(n) = d + 1 gets Unew = P_SU(3)[U + c sum_{nu != mu, n_nu odd}
+// (T+_munu + T-_munu)] (Eq. APE), T+ = U_nu(n) U_mu(n+nu) U_nu(n+mu)^+,
+// T- = U_nu(n-nu)^+ U_mu(n-nu) U_nu(n-nu+mu), read from buffer cur and written
+// to 1 - cur (Jacobi); no other bond changes within a stage.  Stage start
+// (phase 0, d >= 1): the bonds of the previous stage (chi_mu = d) are copied
+// from cur to 1 - cur, so that both buffers agree outside the new stage's bonds.
+template <class T, int NP>
+__global__ void __launch_bounds__(PB_THREADS) k_ape_pb(const __grid_constant__ PBatch<T> B) {
+    const int l = find_block(B.prefix, B.n, blockIdx.x);
+    const ProDesc<T>& D = B.d[l];
+    const ProlongCtl* C = B.ctl + l;
+    const int d = C->d, phase = C->phase, cur = C->cur;
+    if (d >= 3 || (phase == 0 && d == 0)) return;
+    const int idx = (blockIdx.x - B.prefix[l]) * PB_THREADS + threadIdx.x;
+    const Geom& g = D.gf;
     if (idx >= 8 * g.Vh) return;
     const int mp = idx / g.Vh, h = idx - mp * g.Vh, mu = mp >> 1, par = mp & 1;
     int x[4];
     cb_coords(g, par, h, x);
-    if (odd_count_except(x, mu, mu) != d + 1) return;
+    const int chi = odd_count_except(x, mu, mu);
+    const Links<T, NP> Uin = field<T, NP>(D.buf[cur], g), Uout = field<T, NP>(D.buf[cur ^ 1], g);
+    if (phase == 0) {
+        if (chi == d) Uout.store(mu, par, h, Uin.load(mu, par, h));
+        return;
+    }
+    if (chi != d + 1) return;
     const int op = par ^ 1;
     M3<T> M = Uin.load(mu, par, h);
     const int lpm = lex_hop(g, x, mu, +1);
@@ -103,17 +199,26 @@ __global__ void __launch_bounds__(128) k_ape(Links<T, NP> Uin, Links<T, NP> Uout
 #pragma unroll
             for (int j = 0; j < 3; j++) {
                 const Cx<T> sum = tp.e[i][j] + tm.e[i][j];
-                M.e[i][j] = M.e[i][j] + scale(sum, c);
+                M.e[i][j] = M.e[i][j] + scale(sum, B.c);
             }
     }
     Uout.store(mu, par, h, su3_project(M));
 }
 
-// Partial action S_d / beta = sum over plaquettes with chi_munu(n) = d of (1 - Re Tr U_p / 3).
+// S_d / beta = sum over plaquettes with chi_munu(n) = d of (1 - Re Tr U_p / 3)
+// (Eq. smoothing) of the lattice's newest field, and the state update.
 template <class T, int NP>
-__global__ void __launch_bounds__(256) k_partial_action(Links<T, NP> U, Geom g, int d, double* __restrict__ partials) {
+__global__ void __launch_bounds__(PB_SD_THREADS) k_sd_pb(const __grid_constant__ PBatch<T> B) {
+    const int l = find_block(B.sprefix, B.n, blockIdx.x);
+    const ProDesc<T>& D = B.d[l];
+    ProlongCtl* C = B.ctl + l;
+    const int d = C->d, phase = C->phase, cur = C->cur;
+    if (d >= 3) return;
+    const Geom& g = D.gf;
+    const Links<T, NP> U = field<T, NP>(D.buf[phase == 1 ? cur ^ 1 : cur], g);
+    const int nb = B.sprefix[l + 1] - B.sprefix[l], b = blockIdx.x - B.sprefix[l];
     double acc = 0.0;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.V; idx += gridDim.x * blockDim.x) {
+    for (int idx = b * PB_SD_THREADS + threadIdx.x; idx < g.V; idx += nb * PB_SD_THREADS) {
         const int par = idx >= g.Vh, h = idx - par * g.Vh;
         int x[4];
         cb_coords(g, par, h, x);
@@ -125,26 +230,200 @@ __global__ void __launch_bounds__(256) k_partial_action(Links<T, NP> U, Geom g, 
                 if (odd_count_except(x, mu, nu) != d) continue;
                 const int hpm = lex_hop(g, x, mu, +1) >> 1, hpn = lex_hop(g, x, nu, +1) >> 1;
                 const M3<T> a = mul_nn(U.load(mu, par, h), U.load(nu, op, hpm));
-                const M3<T> b = mul_nn(U.load(nu, par, h), U.load(mu, op, hpn));
-                acc += 1.0 - (double)retr_nd(a, b) / 3.0;
+                const M3<T> bb = mul_nn(U.load(nu, par, h), U.load(mu, op, hpn));
+                acc += 1.0 - (double)retr_nd(a, bb) / 3.0;
             }
         }
     }
     acc = block_sum(acc);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    if (threadIdx.x != 0) return;
+    double* part = B.partials + B.sprefix[l];
+    part[b] = acc;
+    __threadfence();
+    if (atomicAdd(B.ticket + l, 1u) != (unsigned)(nb - 1)) return;
+    // the last block of this lattice: every partial is written
+    __threadfence();
+    double S = 0.0;
+    for (int i = 0; i < nb; i++) S += __ldcg(part + i);
+    B.ticket[l] = 0u;
+    if (phase == 0) {
+        C->prev = S;
+        C->it = 0;
+        if (B.max_iter > 0) {
+            C->phase = 1;
+            return;
+        }
+    } else {
+        C->it += 1;
+        C->cur = cur ^ 1;
+        const bool stop = (B.rel_tol > 0.0 && fabs(S - C->prev) <= B.rel_tol * fabs(C->prev)) || C->it >= B.max_iter;
+        if (!stop) {
+            C->prev = S;
+            return;
+        }
+    }
+    C->iters[d] = C->it;
+    C->sd[d] = S;
+    C->d = d + 1;
+    C->phase = 0;
+    if (d + 1 == 3 && !C->counted) {
+        C->counted = 1;
+        atomicAdd(B.ndone, 1);
+    }
+}
+
+// newest field into the lattice's links; iteration counts and final S_d out
+template <class T, int NP>
+__global__ void __launch_bounds__(PB_THREADS) k_finish_pb(const __grid_constant__ PBatch<T> B, int first,
+                                                          int* __restrict__ iters, double* __restrict__ sd) {
+    const int l = find_block(B.prefix, B.n, blockIdx.x);
+    const ProDesc<T>& D = B.d[l];
+    const ProlongCtl* C = B.ctl + l;
+    const int idx = (blockIdx.x - B.prefix[l]) * PB_THREADS + threadIdx.x;
+    if (idx < 3) {
+        iters[3 * (first + l) + idx] = C->d > idx ? C->iters[idx] : (C->d == idx ? C->it : 0);
+        sd[3 * (first + l) + idx] = C->d > idx ? C->sd[idx] : 0.0;
+    }
+    if (C->cur == 0 || idx >= 8 * D.gf.Vh) return;
+    const int mp = idx / D.gf.Vh, h = idx - mp * D.gf.Vh, mu = mp >> 1, par = mp & 1;
+    field<T, NP>(D.buf[0], D.gf).store(mu, par, h, field<T, NP>(D.buf[1], D.gf).load(mu, par, h));
 }
 
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
-static mgq_status partial_action_into(const mgq_lattice* lat, const void* links, int d, double* partials, double* out,
-                                      cudaStream_t st) {
-    const Geom g = make_geom(lat->dims);
-    const int nb = reduction_blocks(g.V, 256);
-    dispatch_prec(lat->prec, [&]<class T, int NP>() {
-        k_partial_action<T, NP><<<nb, 256, 0, st>>>(links_at<T, NP>(const_cast<void*>(links), lat->dims), g, d, partials);
+static int sd_blocks(const Geom& g) {
+    const int b = nblk(g.V, PB_SD_THREADS);
+    return b < PB_SD_MAXBLK ? b : PB_SD_MAXBLK;
+}
+
+// Where the state of a call lives (device): control blocks, tickets, the
+// finished count, partial sums, result staging.
+struct PbState {
+    ProlongCtl* ctl;
+    unsigned* ticket;
+    int* ndone;
+    double* partials;
+    int* iters;
+    double* sd;
+};
+
+template <class T>
+static void fill_pbatch(PBatch<T>& B, const mgq_lattice* coarse, const mgq_lattice* fine, void* const* scratch,
+                        int first, int n, const PbState& S, uint64_t poff, double c, double rel_tol, int max_iter) {
+    B.n = n;
+    B.prefix[0] = 0;
+    B.sprefix[0] = 0;
+    for (int i = 0; i < n; i++) {
+        const mgq_lattice& F = fine[first + i];
+        ProDesc<T>& D = B.d[i];
+        D.buf[0] = reinterpret_cast<Cx<T>*>(F.links);
+        D.buf[1] = reinterpret_cast<Cx<T>*>(scratch[first + i]);
+        D.coarse = reinterpret_cast<Cx<T>*>(coarse[first + i].links);
+        D.gf = make_geom(F.dims);
+        D.gc = make_geom(coarse[first + i].dims);
+        B.prefix[i + 1] = B.prefix[i] + nblk(8L * D.gf.Vh, PB_THREADS);
+        B.sprefix[i + 1] = B.sprefix[i] + sd_blocks(D.gf);
+    }
+    B.ctl = S.ctl + first;
+    B.partials = S.partials + poff;
+    B.ticket = S.ticket + first;
+    B.ndone = S.ndone;
+    B.c = (T)c;
+    B.rel_tol = rel_tol;
+    B.max_iter = max_iter;
+}
+
+// The whole interpolation for n lattices: transfer, then iterations until all
+// lattices finished (budget <= 0: the host reads the finished count every 32
+// iterations) or exactly `budget` iterations (no host synchronisation), then
+// the newest fields into the links and the per-lattice results into S.iters,
+// S.sd (3 per lattice).
+static mgq_status prolong_run(const mgq_lattice* coarse, mgq_lattice* fine, void* const* scratch, int n, double c,
+                              double rel_tol, int max_iter, int budget, const PbState& S, cudaStream_t st) {
+    mgq_status s;
+    if (cudaMemsetAsync(S.ndone, 0, sizeof(int), st) != cudaSuccess) return cuda_check("prolongate: reset");
+    auto each_chunk = [&](auto&& launch) {
+        uint64_t poff = 0;
+        for (int first = 0; first < n; first += PB_CHUNK) {
+            const int m = n - first < PB_CHUNK ? n - first : PB_CHUNK;
+            dispatch_prec(fine[0].prec, [&]<class T, int NP>() {
+                PBatch<T> B;
+                fill_pbatch(B, coarse, fine, scratch, first, m, S, poff, c, rel_tol, max_iter);
+                launch.template operator()<T, NP>(B, first);
+                poff += (uint64_t)B.sprefix[m];
+            });
+        }
+    };
+    each_chunk([&]<class T, int NP>(const PBatch<T>& B, int) {
+        k_transfer_pb<T, NP><<<B.prefix[B.n], PB_THREADS, 0, st>>>(B);
     });
-    launch_final_sum(partials, nb, 1.0, out, st);
-    return cuda_check("partial_action");
+    if ((s = cuda_check("prolongate: transfer"))) return s;
+    auto iteration = [&]() {
+        each_chunk([&]<class T, int NP>(const PBatch<T>& B, int) {
+            k_ape_pb<T, NP><<<B.prefix[B.n], PB_THREADS, 0, st>>>(B);
+            k_sd_pb<T, NP><<<B.sprefix[B.n], PB_SD_THREADS, 0, st>>>(B);
+        });
+    };
+    if (budget > 0) {
+        for (int k = 0; k < budget; k++) iteration();
+        if ((s = cuda_check("prolongate: iterations"))) return s;
+    } else {
+        // at most 3 (max_iter + 1) iterations finish every lattice
+        const long cap = 3L * ((long)max_iter + 1);
+        long done_it = 0;
+        int finished = 0;
+        while (finished < n && done_it < cap) {
+            const int chunk = cap - done_it < 32 ? (int)(cap - done_it) : 32;
+            for (int k = 0; k < chunk; k++) iteration();
+            done_it += chunk;
+            if ((s = cuda_check("prolongate: iterations"))) return s;
+            if (cudaMemcpyAsync(&finished, S.ndone, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return cuda_check("prolongate: poll");
+        }
+    }
+    each_chunk([&]<class T, int NP>(const PBatch<T>& B, int first) {
+        k_finish_pb<T, NP><<<B.prefix[B.n], PB_THREADS, 0, st>>>(B, first, S.iters, S.sd);
+    });
+    return cuda_check("prolongate: finish");
+}
+
+static mgq_status check_pair(const mgq_lattice* coarse, const mgq_lattice* fine, bool need_work, const char* fn) {
+    mgq_status s = check_lattice(coarse, false, fn);
+    if (s) return s;
+    if ((s = check_lattice(fine, need_work, fn))) return s;
+    for (int mu = 0; mu < 4; mu++)
+        if (fine->dims[mu] != 2 * coarse->dims[mu]) return fail(MGQ_EINVAL, "%s: fine extents must be twice the coarse extents", fn);
+    if (fine->prec != coarse->prec) return fail(MGQ_EINVAL, "%s: precisions differ", fn);
+    return MGQ_OK;
+}
+
+// batched workspace: control blocks, tickets, finished count, partials,
+// result staging, then one scratch link field per lattice
+static uint64_t pb_state_bytes(const mgq_lattice* fine, int n) {
+    uint64_t nparts = 0;
+    for (int i = 0; i < n; i++) nparts += (uint64_t)sd_blocks(make_geom(fine[i].dims));
+    return round256((uint64_t)n * sizeof(ProlongCtl)) + round256((uint64_t)n * sizeof(unsigned) + sizeof(int)) +
+           round256(nparts * sizeof(double)) + round256((uint64_t)3 * n * sizeof(int)) +
+           round256((uint64_t)3 * n * sizeof(double));
+}
+
+static PbState pb_state_at(void* work, const mgq_lattice* fine, int n) {
+    uint64_t nparts = 0;
+    for (int i = 0; i < n; i++) nparts += (uint64_t)sd_blocks(make_geom(fine[i].dims));
+    char* p = static_cast<char*>(work);
+    PbState S;
+    S.ctl = reinterpret_cast<ProlongCtl*>(p);
+    p += round256((uint64_t)n * sizeof(ProlongCtl));
+    S.ticket = reinterpret_cast<unsigned*>(p);
+    S.ndone = reinterpret_cast<int*>(p + (uint64_t)n * sizeof(unsigned));
+    p += round256((uint64_t)n * sizeof(unsigned) + sizeof(int));
+    S.partials = reinterpret_cast<double*>(p);
+    p += round256(nparts * sizeof(double));
+    S.iters = reinterpret_cast<int*>(p);
+    p += round256((uint64_t)3 * n * sizeof(int));
+    S.sd = reinterpret_cast<double*>(p);
+    return S;
 }
 
 }  // namespace mgq
@@ -173,62 +452,69 @@ mgq_status mgq_restrict(const mgq_lattice* fine, mgq_lattice* coarse, void* stre
 mgq_status mgq_prolongate(const mgq_lattice* coarse, mgq_lattice* fine, double c, double rel_tol, int max_iter,
                           int* iters_out, double* sd_out, void* stream) {
     Trace trace("mgq_prolongate");
-    mgq_status s = check_lattice(coarse, false, "mgq_prolongate");
+    mgq_status s = check_pair(coarse, fine, true, "mgq_prolongate");
     if (s) return s;
-    if ((s = check_lattice(fine, true, "mgq_prolongate"))) return s;
-    for (int mu = 0; mu < 4; mu++)
-        if (fine->dims[mu] != 2 * coarse->dims[mu])
-            return fail(MGQ_EINVAL, "mgq_prolongate: fine extents must be twice the coarse extents");
-    if (fine->prec != coarse->prec) return fail(MGQ_EINVAL, "mgq_prolongate: precisions differ");
     if (!(c > 0.0) || max_iter < 0) return fail(MGQ_EINVAL, "mgq_prolongate: need c > 0 and max_iter >= 0");
-    const Geom gf = make_geom(fine->dims), gc = make_geom(coarse->dims);
     cudaStream_t st = as_stream(stream);
-    const uint64_t lb = links_bytes(fine);
-    void* bufs[2] = {fine->links, ws_links(fine)};
+    // state in the lattice's workspace: control block, ticket and count in the
+    // scalars, partials in the partial-sum area, the scratch field in its link copy
     double* sc = ws_scalars(fine);
-    double host_sd[2];
-    dispatch_prec(fine->prec, [&]<class T, int NP>() {
-        k_transfer<T, NP><<<nblk(8L * gf.Vh, 128), 128, 0, st>>>(links_of<T, NP>(coarse), gc, links_of<T, NP>(fine), gf);
-    });
-    if ((s = cuda_check("mgq_prolongate: transfer"))) return s;
-    int cur = 0;
-    for (int d = 0; d <= 2; d++) {
-        // both buffers hold the full field: inactive bonds never change during the stage
-        if (cudaMemcpyAsync(bufs[1 - cur], bufs[cur], lb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-            return cuda_check("mgq_prolongate: copy");
-        if ((s = partial_action_into(fine, bufs[cur], d, ws_partials(fine), sc + 20, st))) return s;
-        double prev = 0.0, now = 0.0;
-        if (rel_tol > 0.0) {
-            if ((s = deliver(sc + 20, &prev, 1, st, "mgq_prolongate"))) return s;
-        }
-        int it = 0;
-        while (it < max_iter) {
-            dispatch_prec(fine->prec, [&]<class T, int NP>() {
-                k_ape<T, NP><<<nblk(8L * gf.Vh, 128), 128, 0, st>>>(links_at<T, NP>(bufs[cur], fine->dims),
-                                                                    links_at<T, NP>(bufs[1 - cur], fine->dims), gf, d, (T)c);
-            });
-            if ((s = cuda_check("mgq_prolongate: ape"))) return s;
-            cur = 1 - cur;
-            it++;
-            if (rel_tol > 0.0) {
-                if ((s = partial_action_into(fine, bufs[cur], d, ws_partials(fine), sc + 20, st))) return s;
-                if ((s = deliver(sc + 20, &now, 1, st, "mgq_prolongate"))) return s;
-                const bool done = fabs(now - prev) <= rel_tol * fabs(prev);
-                prev = now;
-                if (done) break;
-            }
-        }
-        if (iters_out) iters_out[d] = it;
-        if (sd_out) {
-            if ((s = partial_action_into(fine, bufs[cur], d, ws_partials(fine), sc + 20, st))) return s;
-            if ((s = deliver(sc + 20, host_sd, 1, st, "mgq_prolongate"))) return s;
-            sd_out[d] = host_sd[0];
-        }
+    PbState S;
+    S.ctl = reinterpret_cast<ProlongCtl*>(sc + 48);
+    S.ticket = reinterpret_cast<unsigned*>(sc + 56);
+    S.ndone = reinterpret_cast<int*>(sc + 57);
+    S.iters = reinterpret_cast<int*>(sc + 58);
+    S.sd = sc + 60;
+    S.partials = ws_partials(fine);
+    void* scratch[1] = {ws_links(fine)};
+    if ((s = prolong_run(coarse, fine, scratch, 1, c, rel_tol, max_iter, 0, S, st))) return s;
+    if (iters_out && (s = deliver_int(S.iters, iters_out, 3, st, "mgq_prolongate"))) return s;
+    if (sd_out && (s = deliver(S.sd, sd_out, 3, st, "mgq_prolongate"))) return s;
+    return MGQ_OK;
+}
+
+uint64_t mgq_prolongate_batched_workspace_bytes(const mgq_lattice* fine, int n) {
+    if (!fine || n < 1) return 0;
+    uint64_t b = pb_state_bytes(fine, n);
+    for (int i = 0; i < n; i++) {
+        const uint64_t lb = links_bytes(&fine[i]);
+        if (!lb) return 0;
+        b += round256(lb);
     }
-    if (cur != 0) {
-        if (cudaMemcpyAsync(fine->links, bufs[cur], lb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-            return cuda_check("mgq_prolongate: copy back");
+    return b;
+}
+
+mgq_status mgq_prolongate_batched(const mgq_lattice* coarse, mgq_lattice* fine, int n, double c, double rel_tol,
+                                  int max_iter, int iter_budget, int* iters_out, double* sd_out, int* n_done_out,
+                                  void* work, uint64_t work_bytes, void* stream) {
+    Trace trace("mgq_prolongate_batched");
+    if (!coarse || !fine || n < 1) return fail(MGQ_EINVAL, "mgq_prolongate_batched: need at least one lattice pair");
+    mgq_status s;
+    for (int i = 0; i < n; i++) {
+        if ((s = check_pair(&coarse[i], &fine[i], false, "mgq_prolongate_batched"))) return s;
+        if (fine[i].prec != fine[0].prec) return fail(MGQ_EINVAL, "mgq_prolongate_batched: all lattices need one precision");
     }
+    if (!(c > 0.0) || max_iter < 0 || iter_budget < 0)
+        return fail(MGQ_EINVAL, "mgq_prolongate_batched: need c > 0, max_iter >= 0, iter_budget >= 0");
+    if (!work || ((uintptr_t)work & 255)) return fail(MGQ_EINVAL, "mgq_prolongate_batched: work NULL or not 256-byte aligned");
+    const uint64_t need = mgq_prolongate_batched_workspace_bytes(fine, n);
+    if (work_bytes < need)
+        return fail(MGQ_ENOMEM, "mgq_prolongate_batched: work has %llu bytes, needs %llu", (unsigned long long)work_bytes,
+                    (unsigned long long)need);
+    cudaStream_t st = as_stream(stream);
+    const PbState S = pb_state_at(work, fine, n);
+    void** scratch = new void*[n];
+    char* p = static_cast<char*>(work) + pb_state_bytes(fine, n);
+    for (int i = 0; i < n; i++) {
+        scratch[i] = p;
+        p += round256(links_bytes(&fine[i]));
+    }
+    s = prolong_run(coarse, fine, scratch, n, c, rel_tol, max_iter, iter_budget, S, st);
+    delete[] scratch;
+    if (s) return s;
+    if (iters_out && (s = deliver_int(S.iters, iters_out, 3 * (size_t)n, st, "mgq_prolongate_batched"))) return s;
+    if (sd_out && (s = deliver(S.sd, sd_out, 3 * (size_t)n, st, "mgq_prolongate_batched"))) return s;
+    if (n_done_out && (s = deliver_int(S.ndone, n_done_out, 1, st, "mgq_prolongate_batched"))) return s;
     return MGQ_OK;
 }
 

@@ -54,3 +54,24 @@ def test_non_unitary_link_is_detected(gpu, orc):
     with pytest.raises(MgqError) as e:
         gpu.mgq_check_unitarity(lat, 1e-10)
     assert e.value.status == 6
+
+
+def test_reunitarize_pass(gpu, orc):
+    """Gram-Schmidt projection of every link (the reunitarisation of the update
+    kernels): FP64 against the oracle's, FP32 with an FP32 or FP64 projection."""
+    dims = [4, 4, 2, 6]
+    rng = np.random.default_rng(9)
+    U = orc.init_links(dims, 1, seed=9)
+    M = U + 0.01 * (rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape))
+    ref = np.stack([[orc.reunit(M[s, mu]) for mu in range(4)] for s in range(M.shape[0])])
+    lat = gpu.Lattice(dims, "f64")
+    lat.from_numpy(M)
+    gpu.mgq_reunitarize(lat)
+    assert np.max(np.abs(lat.to_numpy() - ref)) < 1e-14
+    for prec in ("f32", "f32c12"):
+        for f64 in (False, True):
+            l2 = gpu.Lattice(dims, prec)
+            l2.from_numpy(M)
+            gpu.mgq_reunitarize(l2, fp64_projection=f64)
+            assert np.max(np.abs(l2.to_numpy() - ref)) < 2e-6, (prec, f64)
+            assert gpu.mgq_check_unitarity(l2) < 1e-6
