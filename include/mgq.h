@@ -104,13 +104,21 @@ uint64_t mgq_mom_bytes(const mgq_lattice* lat);
 uint64_t mgq_workspace_bytes(const mgq_lattice* lat);
 
 /* ---- launch tuning ------------------------------------------------------------
- * Threads per block of the checkerboard sub-sweep kernels (heat bath and
- * overrelaxation) of the single-lattice entry points, per
- * storage format: 32, 64, 96 or 128 (the kernels are compiled for at most
- * 128); 128 by default.  Results do not depend on it (one thread per link).
- * Process-wide setting; change it only while no call is being issued.  Set
- * by the autotuner (paper_1510_04675_gb300/tune.py). */
-typedef enum { MGQ_KERNEL_HEATBATH = 0, MGQ_KERNEL_OVERRELAX = 1 } mgq_kernel;
+ * Threads per block, per storage format, of the checkerboard sub-sweep kernels
+ * (heat bath and overrelaxation) of the single-lattice and the batched entry
+ * points and of the APE step of the prolongation: 32, 64, 96 or 128 (the
+ * kernels are compiled for at most 128); 128 by default.  Results do not
+ * depend on it (one thread per link or per active bond).  The force kernel's
+ * shape is structural (eight warps cover the eight (mu, parity) planes of a
+ * 32-site band) and not tuned.  Process-wide setting; change it only while no
+ * call is being issued.  Set by the autotuner (paper_1510_04675_gb300/tune.py). */
+typedef enum {
+    MGQ_KERNEL_HEATBATH = 0,
+    MGQ_KERNEL_OVERRELAX = 1,
+    MGQ_KERNEL_HEATBATH_BATCHED = 2,
+    MGQ_KERNEL_OVERRELAX_BATCHED = 3,
+    MGQ_KERNEL_APE = 4
+} mgq_kernel;
 mgq_status mgq_set_block_size(int kernel, int prec, int threads);
 /* Current value, 0 for an unknown kernel or precision. */
 int mgq_get_block_size(int kernel, int prec);

@@ -14,7 +14,8 @@
 namespace mgq {
 
 constexpr int BATCH_CHUNK = 128;  // lattices per launch (kernel-parameter table)
-constexpr int BATCH_THREADS = 128;
+constexpr int BATCH_THREADS = 128;     // the kernels' maximal block size
+constexpr int BATCH_MIN_THREADS = 32;  // the smallest tunable block size (sizes the partial sums)
 
 template <class T>
 struct LatDesc {
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4)
     pdl_launch_dependents();
     const int l = find_lattice(B, blockIdx.x);
     const LatDesc<T>& d = B.d[l];
-    const int h = (blockIdx.x - B.prefix[l]) * BATCH_THREADS + threadIdx.x;
+    const int h = (blockIdx.x - B.prefix[l]) * (int)blockDim.x + threadIdx.x;
     pdl_wait();
     if (h >= d.g.Vh) return;
     const Geom g = geom_of(d);
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4) k_overr
     pdl_launch_dependents();
     const int l = find_lattice(B, blockIdx.x);
     const LatDesc<T>& d = B.d[l];
-    const int h = (blockIdx.x - B.prefix[l]) * BATCH_THREADS + threadIdx.x;
+    const int h = (blockIdx.x - B.prefix[l]) * (int)blockDim.x + threadIdx.x;
     pdl_wait();
     if (h >= d.g.Vh) return;
     const Geom g = geom_of(d);
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4)
     pdl_launch_dependents();
     const int l = find_lattice(B, blockIdx.x);
     const LatDesc<T>& d = B.d[l];
-    const int h = (blockIdx.x - B.prefix[l]) * BATCH_THREADS + threadIdx.x;
+    const int h = (blockIdx.x - B.prefix[l]) * (int)blockDim.x + threadIdx.x;
     pdl_wait();
     double acc = 0.0;
     if (h < d.g.Vh) {
@@ -189,7 +190,7 @@ uint64_t batch_partials(const mgq_lattice* lats, int n) {
     uint64_t nb = 0;
     for (int i = 0; i < n; i++) {
         const Geom g = make_geom(lats[i].dims);
-        nb += 2 * (uint64_t)((g.Vh + BATCH_THREADS - 1) / BATCH_THREADS);
+        nb += 2 * (uint64_t)((g.Vh + BATCH_MIN_THREADS - 1) / BATCH_MIN_THREADS);
     }
     return nb;
 }
@@ -239,17 +240,20 @@ mgq_status mgq_update_sweeps_batched(mgq_lattice* lats, int n_lat, const double*
         for (int first = 0; first < n_lat; first += BATCH_CHUNK) {
             const int n = (n_lat - first < BATCH_CHUNK) ? n_lat - first : BATCH_CHUNK;
             dispatch_prec(lats[0].prec, [&]<class T, int NP>() {
-                Batch<T> Bl;
-                fill_batch(Bl, lats, betas, first, n, BATCH_THREADS, true);
-                const int nblocks = Bl.prefix[n];
+                const int bh = block_size(MGQ_KERNEL_HEATBATH_BATCHED, lats[0].prec);
+                const int bo = block_size(MGQ_KERNEL_OVERRELAX_BATCHED, lats[0].prec);
+                Batch<T> Bl, Bo;
+                fill_batch(Bl, lats, betas, first, n, bh, true);
+                fill_batch(Bo, lats, betas, first, n, bo, true);
+                const int nblocks = Bl.prefix[n], oblocks = Bo.prefix[n];
                 for (int mu = 0; mu < 4; mu++)
                     for (int par = 0; par < 2; par++)
                         dispatch_mu(mu, [&]<int MU>() {
                             if (n_hb == 1)
-                                launch_pdl(k_heatbath_batched<T, NP, MU, true>, nblocks, BATCH_THREADS, st, Bl, par,
+                                launch_pdl(k_heatbath_batched<T, NP, MU, true>, nblocks, bh, st, Bl, par,
                                            (uint32_t)(sweep & 0xffffffffu), (uint32_t)(sweep >> 32), n_hb);
                             else
-                                launch_pdl(k_heatbath_batched<T, NP, MU, false>, nblocks, BATCH_THREADS, st, Bl, par,
+                                launch_pdl(k_heatbath_batched<T, NP, MU, false>, nblocks, bh, st, Bl, par,
                                            (uint32_t)(sweep & 0xffffffffu), (uint32_t)(sweep >> 32), n_hb);
                         });
                 // with a plaquette record, the last overrelaxation sweep's
@@ -259,15 +263,15 @@ mgq_status mgq_update_sweeps_batched(mgq_lattice* lats, int n_lat, const double*
                     for (int mu = 0; mu < 4; mu++)
                         for (int par = 0; par < 2; par++) {
                             if (fold && k == n_or - 1 && mu == 3) {
-                                launch_pdl(k_overrelax_batched_last<T, NP>, nblocks, BATCH_THREADS, st, Bl, par, partials);
+                                launch_pdl(k_overrelax_batched_last<T, NP>, oblocks, bo, st, Bo, par, partials);
                                 continue;
                             }
                             dispatch_mu(mu, [&]<int MU>() {
-                                launch_pdl(k_overrelax_batched<T, NP, MU>, nblocks, BATCH_THREADS, st, Bl, par);
+                                launch_pdl(k_overrelax_batched<T, NP, MU>, oblocks, bo, st, Bo, par);
                             });
                         }
                 if (fold)
-                    k_overrelax_batched_last_final<T><<<n, 256, 0, st>>>(Bl, partials,
+                    k_overrelax_batched_last_final<T><<<n, 256, 0, st>>>(Bo, partials,
                                                                          results + (size_t)i * n_lat + first);
             });
             if ((s = cuda_check("mgq_update_sweeps_batched"))) return s;

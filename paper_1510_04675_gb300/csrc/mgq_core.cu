@@ -352,7 +352,10 @@ static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 // Launch shape of the sub-sweep kernels per (kernel, precision): threads per
 // block, at most the 128 the kernels are compiled for.  Set by
 // mgq_set_block_size (the autotuner); 128 by default.
-static int g_block[2][3] = {{128, 128, 128}, {128, 128, 128}};
+static int g_block[MGQ_NKERNELS][3] = {{128, 128, 128}, {128, 128, 128}, {128, 128, 128}, {128, 128, 128},
+                                      {128, 128, 128}};
+
+int block_size(int kernel, int prec) { return g_block[kernel][prec]; }
 
 mgq_status heatbath_subsweep(mgq_lattice* lat, double beta, uint64_t sweep, int n_hb, int mu, int par,
                              uint8_t* dec, cudaStream_t st) {
@@ -446,7 +449,7 @@ uint64_t mgq_mom_bytes(const mgq_lattice* lat) { return alg_bytes(lat); }
 uint64_t mgq_workspace_bytes(const mgq_lattice* lat) { return workspace_bytes(lat); }
 
 mgq_status mgq_set_block_size(int kernel, int prec, int threads) {
-    if (kernel < 0 || kernel > 1) return fail(MGQ_EINVAL, "mgq_set_block_size: unknown kernel %d", kernel);
+    if (kernel < 0 || kernel >= MGQ_NKERNELS) return fail(MGQ_EINVAL, "mgq_set_block_size: unknown kernel %d", kernel);
     if (prec < MGQ_F64 || prec > MGQ_F32_C12) return fail(MGQ_EINVAL, "mgq_set_block_size: prec %d invalid", prec);
     if (threads < 32 || threads > 128 || (threads & 31))
         return fail(MGQ_EINVAL, "mgq_set_block_size: threads must be 32, 64, 96 or 128");
@@ -455,7 +458,7 @@ mgq_status mgq_set_block_size(int kernel, int prec, int threads) {
 }
 
 int mgq_get_block_size(int kernel, int prec) {
-    if (kernel < 0 || kernel > 1 || prec < MGQ_F64 || prec > MGQ_F32_C12) return 0;
+    if (kernel < 0 || kernel >= MGQ_NKERNELS || prec < MGQ_F64 || prec > MGQ_F32_C12) return 0;
     return g_block[kernel][prec];
 }
 

@@ -59,6 +59,9 @@ bool is_device_ptr(const void* p);
 
 // Number of blocks used by the site-parallel reduction kernels.
 int reduction_blocks(int V, int threads);
+// threads per block of a tunable kernel (mgq_kernel) for a precision
+constexpr int MGQ_NKERNELS = 5;
+int block_size(int kernel, int prec);
 
 // Sums n partials in a fixed order into out[0] * scale (device).
 void launch_final_sum(const double* partials, int n, double scale, double* out, cudaStream_t st);

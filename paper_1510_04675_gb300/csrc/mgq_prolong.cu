@@ -9,6 +9,10 @@ namespace mgq {
 
 // P_SU(3)(M): Gram-Schmidt start W, then NPASS passes over the subgroups
 // (0,1), (0,2), (1,2) of W <- R W with R = R(w/|w|) maximising Re Tr(R W M^+).
+// FP64 runs exactly NPASS passes (the oracle's definition).  FP32 stops after a
+// pass whose three rotations all round to the identity (|r - 1| below half an
+// FP32 unit in the last place of 1 in every component): later passes would
+// not move W by more than FP32 rounding.
 template <class T>
 __device__ __forceinline__ M3<T> su3_project(const M3<T>& M) {
     constexpr int NPASS = 8;
@@ -16,6 +20,7 @@ __device__ __forceinline__ M3<T> su3_project(const M3<T>& M) {
     reunitarize(W);
 #pragma unroll 1
     for (int pass = 0; pass < NPASS; pass++) {
+        bool moved = false;
 #pragma unroll
         for (int s = 0; s < 3; s++) {
             const int i = (s == 2) ? 1 : 0, j = (s == 0) ? 1 : 2;
@@ -26,7 +31,12 @@ __device__ __forceinline__ M3<T> su3_project(const M3<T>& M) {
             if (!(xi >= tiny_norm<T>())) continue;
             const T inv = T(1) / xi;
             const T r[4] = {w[0] * inv, w[1] * inv, w[2] * inv, w[3] * inv};
+            if constexpr (sizeof(T) == 4)
+                moved = moved || fabsf(r[1]) > 3e-8f || fabsf(r[2]) > 3e-8f || fabsf(r[3]) > 3e-8f;
             left_su2(W, i, j, r);
+        }
+        if constexpr (sizeof(T) == 4) {
+            if (!moved) break;
         }
     }
     return W;
@@ -89,7 +99,7 @@ static_assert(sizeof(ProlongCtl) == 64, "control block layout");
 constexpr int PB_CHUNK = 64;       // lattices per launch (kernel-parameter table)
 constexpr int PB_THREADS = 128;
 constexpr int PB_SD_THREADS = 256;
-constexpr int PB_SD_MAXBLK = 64;   // partial-action blocks per lattice
+constexpr int PB_SD_MAXBLK = 512;  // partial-action blocks per lattice
 
 template <class T>
 struct ProDesc {
@@ -101,7 +111,8 @@ struct ProDesc {
 template <class T>
 struct PBatch {
     int n;
-    int prefix[PB_CHUNK + 1];   // blocks of the per-bond kernels (8 Vh_f bonds each)
+    int prefix[PB_CHUNK + 1];   // blocks of the all-bond kernels (8 Vh_f bonds each)
+    int aprefix[PB_CHUNK + 1];  // blocks of the APE kernel (the largest stage set, 24 V_c bonds)
     int sprefix[PB_CHUNK + 1];  // blocks of the partial-action kernel
     ProDesc<T> d[PB_CHUNK];
     ProlongCtl* ctl;            // [n]
@@ -156,6 +167,82 @@ __global__ void __launch_bounds__(PB_THREADS) k_transfer_pb(const __grid_constan
     field<T, NP>(D.buf[1], D.gf).store(mu, par, h, u);
 }
 
+// ---- the bonds and plaquettes a stage touches, enumerated without gaps
+// Every fine site is n = 2y + b with y a site of the half-extent lattice gc
+// and b in {0,1}^4 its parity pattern; chi_mu(n) counts the odd b outside mu
+// and chi_munu(n) those outside mu and nu (Sec. III).  Bonds with chi_mu = k:
+// b_mu free and exactly k of the three other b odd, 2 C(3,k) patterns per
+// direction, 8 C(3,k) V_c bonds in all (V_c = V/16).  Plaquettes with
+// chi_munu = d: b_mu, b_nu free and d of the two other b odd, 4 C(2,d)
+// patterns per plane, 24 C(2,d) V_c in all.  A thread per bond (plaquette)
+// of the set keeps every lane of a warp busy; looping over all bonds would
+// leave 5/8 to 7/8 of the lanes idle.
+
+__device__ __forceinline__ int binom3(int k) { return (k == 0 || k == 3) ? 1 : 3; }
+
+// j-th k-element subset of three slots, as a bit mask
+__device__ __forceinline__ int subset3(int k, int j) {
+    if (k == 0) return 0;
+    if (k == 3) return 7;
+    if (k == 1) return 1 << j;
+    return j == 0 ? 3 : (j == 1 ? 5 : 6);
+}
+
+// coordinates of lexicographic site y of gc
+__device__ __forceinline__ void lex_coords(const Geom& gc, int y, int yc[4]) {
+    const int r0 = div_L(gc, 0, y);
+    yc[0] = y - r0 * gc.L[0];
+    const int r1 = div_L(gc, 1, r0);
+    yc[1] = r0 - r1 * gc.L[1];
+    yc[3] = div_L(gc, 2, r1);
+    yc[2] = r1 - yc[3] * gc.L[2];
+}
+
+// fine site 2y + b with b given on the directions: b_a, b_b on the two chosen
+// directions a < b and the bits of `mask` on the remaining ones in order
+__device__ __forceinline__ void fine_site(const int yc[4], int a, int ba, int b, int bb, int mask, int x[4]) {
+    int o = 0;
+#pragma unroll
+    for (int dd = 0; dd < 4; dd++) {
+        int bit;
+        if (dd == a) bit = ba;
+        else if (dd == b) bit = bb;
+        else {
+            bit = (mask >> o) & 1;
+            o++;
+        }
+        x[dd] = 2 * yc[dd] + bit;
+    }
+}
+
+__device__ __forceinline__ int n_bonds(const Geom& gc, int k) { return 8 * binom3(k) * gc.V; }
+__device__ __forceinline__ int n_plaqs(const Geom& gc, int d) { return 24 * (d == 1 ? 2 : 1) * gc.V; }
+
+// bond t of the set chi_mu = k: direction mu, fine site x
+__device__ __forceinline__ void bond_of(const Geom& gc, int k, int t, int& mu, int x[4]) {
+    const int y = t % gc.V, r = t / gc.V;
+    const int npat = 2 * binom3(k);
+    mu = r / npat;
+    const int p = r - mu * npat;
+    int yc[4];
+    lex_coords(gc, y, yc);
+    fine_site(yc, mu, p & 1, -1, 0, subset3(k, p >> 1), x);
+}
+
+// plaquette t of the set chi_munu = d: plane (mu, nu), fine site x
+__device__ __forceinline__ void plaq_of(const Geom& gc, int d, int t, int& mu, int& nu, int x[4]) {
+    const int y = t % gc.V, r = t / gc.V;
+    const int npat = 4 * (d == 1 ? 2 : 1);
+    const int pl = r / npat, p = r - pl * npat;
+    mu = pl < 3 ? 0 : (pl < 5 ? 1 : 2);
+    nu = pl < 3 ? pl + 1 : (pl < 5 ? pl - 1 : 3);
+    const int j = p >> 2;
+    const int mask = d == 0 ? 0 : (d == 2 ? 3 : (1 << j));
+    int yc[4];
+    lex_coords(gc, y, yc);
+    fine_site(yc, mu, p & 1, nu, (p >> 1) & 1, mask, x);
+}
+
 // One iteration's bond work.  Stepping (phase 1): every bond with
 // chi_mu(n) = d + 1 gets Unew = P_SU(3)[U + c sum_{nu != mu, n_nu odd}
 // (T+_munu + T-_munu)] (Eq. APE), T+ = U_nu(n) U_mu(n+nu) U_nu(n+mu)^+,
@@ -165,24 +252,23 @@ __global__ void __launch_bounds__(PB_THREADS) k_transfer_pb(const __grid_constan
 // from cur to 1 - cur, so that both buffers agree outside the new stage's bonds.
 template <class T, int NP>
 __global__ void __launch_bounds__(PB_THREADS) k_ape_pb(const __grid_constant__ PBatch<T> B) {
-    const int l = find_block(B.prefix, B.n, blockIdx.x);
+    const int l = find_block(B.aprefix, B.n, blockIdx.x);
     const ProDesc<T>& D = B.d[l];
     const ProlongCtl* C = B.ctl + l;
     const int d = C->d, phase = C->phase, cur = C->cur;
     if (d >= 3 || (phase == 0 && d == 0)) return;
-    const int idx = (blockIdx.x - B.prefix[l]) * PB_THREADS + threadIdx.x;
+    const int k = phase == 0 ? d : d + 1;  // chi_mu of the bonds this iteration touches
+    const int t = (blockIdx.x - B.aprefix[l]) * (int)blockDim.x + threadIdx.x;
+    if (t >= n_bonds(D.gc, k)) return;
     const Geom& g = D.gf;
-    if (idx >= 8 * g.Vh) return;
-    const int mp = idx / g.Vh, h = idx - mp * g.Vh, mu = mp >> 1, par = mp & 1;
-    int x[4];
-    cb_coords(g, par, h, x);
-    const int chi = odd_count_except(x, mu, mu);
+    int mu, x[4];
+    bond_of(D.gc, k, t, mu, x);
+    const int par = (x[0] + x[1] + x[2] + x[3]) & 1, h = lex_of(g, x) >> 1;
     const Links<T, NP> Uin = field<T, NP>(D.buf[cur], g), Uout = field<T, NP>(D.buf[cur ^ 1], g);
     if (phase == 0) {
-        if (chi == d) Uout.store(mu, par, h, Uin.load(mu, par, h));
+        Uout.store(mu, par, h, Uin.load(mu, par, h));
         return;
     }
-    if (chi != d + 1) return;
     const int op = par ^ 1;
     M3<T> M = Uin.load(mu, par, h);
     const int lpm = lex_hop(g, x, mu, +1);
@@ -205,6 +291,31 @@ __global__ void __launch_bounds__(PB_THREADS) k_ape_pb(const __grid_constant__ P
     Uout.store(mu, par, h, su3_project(M));
 }
 
+// Re Tr of the plaquette U_mu(x) U_nu(x+mu) (U_nu(x) U_mu(x+nu))^+.  FP32: from
+// rows 0, 1 of a = U_mu(x) U_nu(x+mu) and b = U_nu(x) U_mu(x+nu), with
+// s_ij = row_i(a) . conj(row_j(b)), Re Tr(a b^+) = Re[s00 + s11 + conj(s00 s11 -
+// s01 s10)] (row 2 of an SU(3) matrix is conj(row0 x row1); Binet-Cauchy).
+// FP64: full products (the oracle's operations).
+template <class T, int NP>
+__device__ __forceinline__ T plaq_retr(const Links<T, NP>& U, int mu, int nu, int par, int op, int h, int hpm, int hpn) {
+    if constexpr (sizeof(T) == 4) {
+        const M3<T> a = mul_nn_2(U.load_rows(mu, par, h), U.load(nu, op, hpm));
+        const M3<T> b = mul_nn_2(U.load_rows(nu, par, h), U.load(mu, op, hpn));
+        Cx<T> sij[2][2];
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 2; j++)
+                sij[i][j] = mulc(a.e[i][0], b.e[j][0]) + mulc(a.e[i][1], b.e[j][1]) + mulc(a.e[i][2], b.e[j][2]);
+        const Cx<T> dd = sij[0][0] * sij[1][1] - sij[0][1] * sij[1][0];
+        return sij[0][0].re + sij[1][1].re + dd.re;
+    } else {
+        const M3<T> a = mul_nn(U.load(mu, par, h), U.load(nu, op, hpm));
+        const M3<T> b = mul_nn(U.load(nu, par, h), U.load(mu, op, hpn));
+        return retr_nd(a, b);
+    }
+}
+
 // S_d / beta = sum over plaquettes with chi_munu(n) = d of (1 - Re Tr U_p / 3)
 // (Eq. smoothing) of the lattice's newest field, and the state update.
 template <class T, int NP>
@@ -217,34 +328,31 @@ __global__ void __launch_bounds__(PB_SD_THREADS) k_sd_pb(const __grid_constant__
     const Geom& g = D.gf;
     const Links<T, NP> U = field<T, NP>(D.buf[phase == 1 ? cur ^ 1 : cur], g);
     const int nb = B.sprefix[l + 1] - B.sprefix[l], b = blockIdx.x - B.sprefix[l];
+    const int np = n_plaqs(D.gc, d);
     double acc = 0.0;
-    for (int idx = b * PB_SD_THREADS + threadIdx.x; idx < g.V; idx += nb * PB_SD_THREADS) {
-        const int par = idx >= g.Vh, h = idx - par * g.Vh;
-        int x[4];
-        cb_coords(g, par, h, x);
-        const int op = par ^ 1;
-#pragma unroll
-        for (int mu = 0; mu < 3; mu++) {
-#pragma unroll
-            for (int nu = mu + 1; nu < 4; nu++) {
-                if (odd_count_except(x, mu, nu) != d) continue;
-                const int hpm = lex_hop(g, x, mu, +1) >> 1, hpn = lex_hop(g, x, nu, +1) >> 1;
-                const M3<T> a = mul_nn(U.load(mu, par, h), U.load(nu, op, hpm));
-                const M3<T> bb = mul_nn(U.load(nu, par, h), U.load(mu, op, hpn));
-                acc += 1.0 - (double)retr_nd(a, bb) / 3.0;
-            }
-        }
+    for (int t = b * PB_SD_THREADS + threadIdx.x; t < np; t += nb * PB_SD_THREADS) {
+        int mu, nu, x[4];
+        plaq_of(D.gc, d, t, mu, nu, x);
+        const int par = (x[0] + x[1] + x[2] + x[3]) & 1, h = lex_of(g, x) >> 1, op = par ^ 1;
+        const int hpm = lex_hop(g, x, mu, +1) >> 1, hpn = lex_hop(g, x, nu, +1) >> 1;
+        acc += 1.0 - (double)plaq_retr(U, mu, nu, par, op, h, hpm, hpn) / 3.0;
     }
     acc = block_sum(acc);
-    if (threadIdx.x != 0) return;
     double* part = B.partials + B.sprefix[l];
-    part[b] = acc;
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+        part[b] = acc;
+        __threadfence();
+        last = atomicAdd(B.ticket + l, 1u) == (unsigned)(nb - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    // the last block of this lattice: every partial is written; a fixed-order sum
     __threadfence();
-    if (atomicAdd(B.ticket + l, 1u) != (unsigned)(nb - 1)) return;
-    // the last block of this lattice: every partial is written
-    __threadfence();
-    double S = 0.0;
-    for (int i = 0; i < nb; i++) S += __ldcg(part + i);
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nb; i += PB_SD_THREADS) v += __ldcg(part + i);
+    const double S = block_sum(v);
+    if (threadIdx.x != 0) return;
     B.ticket[l] = 0u;
     if (phase == 0) {
         C->prev = S;
@@ -291,9 +399,22 @@ __global__ void __launch_bounds__(PB_THREADS) k_finish_pb(const __grid_constant_
 
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
-static int sd_blocks(const Geom& g) {
-    const int b = nblk(g.V, PB_SD_THREADS);
-    return b < PB_SD_MAXBLK ? b : PB_SD_MAXBLK;
+// partial-action blocks of one lattice: one block per 256 plaquettes of the
+// largest set (48 V_c = 3 V) for a lattice alone, up to PB_SD_MAXBLK; in a call
+// over many lattices the lattice's share of about 4096 blocks, so that the
+// blocks stay large when there is parallelism across lattices
+static int sd_blocks(const Geom& g, double total_sites) {
+    const long full = nblk(3L * g.V, PB_SD_THREADS);
+    long b = (long)((4096.0 * g.V + total_sites - 1.0) / total_sites);
+    if (b > full) b = full;
+    if (b > PB_SD_MAXBLK) b = PB_SD_MAXBLK;
+    return b < 1 ? 1 : (int)b;
+}
+
+static double total_sites(const mgq_lattice* fine, int n) {
+    double v = 0.0;
+    for (int i = 0; i < n; i++) v += (double)fine[i].dims[0] * fine[i].dims[1] * fine[i].dims[2] * fine[i].dims[3];
+    return v;
 }
 
 // Where the state of a call lives (device): control blocks, tickets, the
@@ -309,9 +430,11 @@ struct PbState {
 
 template <class T>
 static void fill_pbatch(PBatch<T>& B, const mgq_lattice* coarse, const mgq_lattice* fine, void* const* scratch,
-                        int first, int n, const PbState& S, uint64_t poff, double c, double rel_tol, int max_iter) {
+                        int first, int n, const PbState& S, uint64_t poff, double c, double rel_tol, int max_iter,
+                        double tsites) {
     B.n = n;
     B.prefix[0] = 0;
+    B.aprefix[0] = 0;
     B.sprefix[0] = 0;
     for (int i = 0; i < n; i++) {
         const mgq_lattice& F = fine[first + i];
@@ -322,7 +445,8 @@ static void fill_pbatch(PBatch<T>& B, const mgq_lattice* coarse, const mgq_latti
         D.gf = make_geom(F.dims);
         D.gc = make_geom(coarse[first + i].dims);
         B.prefix[i + 1] = B.prefix[i] + nblk(8L * D.gf.Vh, PB_THREADS);
-        B.sprefix[i + 1] = B.sprefix[i] + sd_blocks(D.gf);
+        B.aprefix[i + 1] = B.aprefix[i] + nblk(24L * D.gc.V, block_size(MGQ_KERNEL_APE, F.prec));
+        B.sprefix[i + 1] = B.sprefix[i] + sd_blocks(D.gf, tsites);
     }
     B.ctl = S.ctl + first;
     B.partials = S.partials + poff;
@@ -341,6 +465,7 @@ static void fill_pbatch(PBatch<T>& B, const mgq_lattice* coarse, const mgq_latti
 static mgq_status prolong_run(const mgq_lattice* coarse, mgq_lattice* fine, void* const* scratch, int n, double c,
                               double rel_tol, int max_iter, int budget, const PbState& S, cudaStream_t st) {
     mgq_status s;
+    const double tsites = total_sites(fine, n);
     if (cudaMemsetAsync(S.ndone, 0, sizeof(int), st) != cudaSuccess) return cuda_check("prolongate: reset");
     auto each_chunk = [&](auto&& launch) {
         uint64_t poff = 0;
@@ -348,7 +473,7 @@ static mgq_status prolong_run(const mgq_lattice* coarse, mgq_lattice* fine, void
             const int m = n - first < PB_CHUNK ? n - first : PB_CHUNK;
             dispatch_prec(fine[0].prec, [&]<class T, int NP>() {
                 PBatch<T> B;
-                fill_pbatch(B, coarse, fine, scratch, first, m, S, poff, c, rel_tol, max_iter);
+                fill_pbatch(B, coarse, fine, scratch, first, m, S, poff, c, rel_tol, max_iter, tsites);
                 launch.template operator()<T, NP>(B, first);
                 poff += (uint64_t)B.sprefix[m];
             });
@@ -360,7 +485,7 @@ static mgq_status prolong_run(const mgq_lattice* coarse, mgq_lattice* fine, void
     if ((s = cuda_check("prolongate: transfer"))) return s;
     auto iteration = [&]() {
         each_chunk([&]<class T, int NP>(const PBatch<T>& B, int) {
-            k_ape_pb<T, NP><<<B.prefix[B.n], PB_THREADS, 0, st>>>(B);
+            k_ape_pb<T, NP><<<B.aprefix[B.n], block_size(MGQ_KERNEL_APE, fine[0].prec), 0, st>>>(B);
             k_sd_pb<T, NP><<<B.sprefix[B.n], PB_SD_THREADS, 0, st>>>(B);
         });
     };
@@ -402,7 +527,8 @@ static mgq_status check_pair(const mgq_lattice* coarse, const mgq_lattice* fine,
 // result staging, then one scratch link field per lattice
 static uint64_t pb_state_bytes(const mgq_lattice* fine, int n) {
     uint64_t nparts = 0;
-    for (int i = 0; i < n; i++) nparts += (uint64_t)sd_blocks(make_geom(fine[i].dims));
+    const double ts = total_sites(fine, n);
+    for (int i = 0; i < n; i++) nparts += (uint64_t)sd_blocks(make_geom(fine[i].dims), ts);
     return round256((uint64_t)n * sizeof(ProlongCtl)) + round256((uint64_t)n * sizeof(unsigned) + sizeof(int)) +
            round256(nparts * sizeof(double)) + round256((uint64_t)3 * n * sizeof(int)) +
            round256((uint64_t)3 * n * sizeof(double));
@@ -410,7 +536,8 @@ static uint64_t pb_state_bytes(const mgq_lattice* fine, int n) {
 
 static PbState pb_state_at(void* work, const mgq_lattice* fine, int n) {
     uint64_t nparts = 0;
-    for (int i = 0; i < n; i++) nparts += (uint64_t)sd_blocks(make_geom(fine[i].dims));
+    const double ts = total_sites(fine, n);
+    for (int i = 0; i < n; i++) nparts += (uint64_t)sd_blocks(make_geom(fine[i].dims), ts);
     char* p = static_cast<char*>(work);
     PbState S;
     S.ctl = reinterpret_cast<ProlongCtl*>(p);

@@ -97,9 +97,11 @@ def test_block_size_settings(mgqlib):
     assert mgqlib.mgq_get_block_size(0, 2) == 128
     assert mgqlib.mgq_set_block_size(0, 2, 64) == 0 and mgqlib.mgq_get_block_size(0, 2) == 64
     assert mgqlib.mgq_set_block_size(0, 2, 128) == 0
-    for bad in [(0, 2, 48), (0, 2, 256), (2, 0, 64), (1, 5, 64)]:
+    for bad in [(0, 2, 48), (0, 2, 256), (5, 0, 64), (-1, 0, 64), (1, 5, 64)]:
         assert mgqlib.mgq_set_block_size(*bad) == 1
     assert mgqlib.mgq_get_block_size(7, 0) == 0
+    for k in range(5):  # single-lattice and batched sub-sweeps, APE
+        assert mgqlib.mgq_get_block_size(k, 1) == 128
 
 
 def test_adaptive_flow_host_helpers(mgqlib):

@@ -41,3 +41,19 @@ def test_jsonl_log_records_and_cli_rejects_bad_flags():
     assert WorkflowConfig().coarse == [8, 8, 8, 8]
     with pytest.raises(SystemExit):
         main(["--flow", "sideways"])
+
+
+def test_tau_int_of_an_ar1_process():
+    """The windowed integrated autocorrelation time used by the chain
+    comparisons: an AR(1) process x_t = r x_{t-1} + e_t has tau_int =
+    (1 + r) / (2 (1 - r))."""
+    from test_gpu_update import _tau_int
+
+    rng = np.random.default_rng(5)
+    for r in (0.0, 0.5, 0.8):
+        x = np.zeros(40000)
+        e = rng.standard_normal(x.size)
+        for t in range(1, x.size):
+            x[t] = r * x[t - 1] + e[t]
+        want = (1 + r) / (2 * (1 - r))
+        assert abs(_tau_int(x) - want) < 0.12 * want + 0.05, (r, _tau_int(x), want)

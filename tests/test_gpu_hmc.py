@@ -39,6 +39,23 @@ def test_force_fp32(gpu, orc, prec):
     assert np.max(np.abs(got - ref)) < 2e-5 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32c12", 2e-5)])
+def test_momentum_step_parity(gpu, orc, prec, tol):
+    """The leapfrog's fused P-step: P <- P + eps F(U) on lat.mom (Sec. IV.D)."""
+    dims, beta, eps = [6, 4, 4, 8], 5.9, 0.037
+    U = _thermal(orc, dims, beta, 5)
+    rng = np.random.default_rng(6)
+    P0 = rng.standard_normal((U.shape[0], 4, 8))
+    lat = gpu.Lattice(dims, prec, with_mom=True)
+    lat.from_numpy(U)
+    from paper_1510_04675_gb300.api import alg_from_numpy
+
+    lat.mom.view(lat.real_dtype()).copy_(alg_from_numpy(lat, P0))
+    gpu.mgq_hmc_momentum_step(lat, beta, eps)
+    ref = P0 + eps * orc.force(U, dims, beta)
+    assert np.max(np.abs(lat.mom_numpy() - ref)) < tol * max(1.0, np.max(np.abs(ref)))
+
+
 def test_trajectory_parity_fp64(gpu, orc):
     dims, beta = [4, 4, 4, 4], 5.7
     U = _thermal(orc, dims, beta, 5)
