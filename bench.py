@@ -769,6 +769,7 @@ def run_mgq(args, dims, world, rank, local):
                              "algorithmic_bytes_per_launch": b_step, "bytes_per_link": lb + 16 * rb,
                              "hbm_gbs": b_step / (ms_step * 1e-3) / 1e9,
                              "hbm_frac": b_step / (ms_step * 1e-3) / 1e9 / peak,
+                             "traffic": traffic_from_profiles("k_force", tag),
                              "roofline": alu_roof("k_force", 4 * V, ms_step)}
         out["force_gbs"] = b_force / (ms_force * 1e-3) / 1e9
         out["force_ms"] = ms_force

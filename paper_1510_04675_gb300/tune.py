@@ -69,6 +69,7 @@ def autotune(lat: "api.Lattice", beta: float = 6.0, candidates: Sequence[int] = 
         choice = cache[key]
     else:
         scratch = api.copy_lattice(lat)
+        plaq = torch.zeros(1, dtype=torch.float64, device=lat.device)
         choice, timings = {}, {}
         for kernel in ("heatbath", "overrelax"):
             best = None
@@ -77,7 +78,10 @@ def autotune(lat: "api.Lattice", beta: float = 6.0, candidates: Sequence[int] = 
                 if kernel == "heatbath":
                     ms = _time(lambda: api.mgq_heatbath_sweep(scratch, beta, 0, 1), reps)
                 else:
-                    ms = _time(lambda: api.mgq_overrelax_sweep(scratch), reps)
+                    # the overrelaxation sweeps of a compound sweep: plain ones and the
+                    # last one, which measures the plaquette with the same block size
+                    ms = _time(lambda: [api.mgq_overrelax_sweep(scratch) for _ in range(3)]
+                               + [api.mgq_overrelax_sweep_plaquette(scratch, out=plaq)], reps)
                 timings[f"{kernel}:{bs}"] = ms
                 if best is None or ms < best[1]:
                     best = (bs, ms)
