@@ -1009,6 +1009,11 @@ double orc_partial_action(const double* U, const int* dims, int d)
  * those with delta_{d, chi_munu(n)} = 1, i.e. n_nu odd.
  * T+_munu(n) = U_nu(n) U_mu(n+nu) U_nu(n+mu)^+
  * T-_munu(n) = U_nu(n-nu)^+ U_mu(n-nu) U_nu(n-nu+mu)
+ * (the printed T- carries a dagger on its last factor, which is not gauge
+ * covariant; the backward staple above is).  Pinned by: a pure-gauge field is
+ * a fixed point of every stage; the step commutes with local gauge
+ * transforms; on abelian links diag(e^{it}, e^{-it}, 1) it is U(1) APE
+ * smearing of t (tests/test_oracle_prolong.py).
  */
 static void ape_step(double* U, double* Unew, const lat_t* g, int d, double c, int n_pass)
 {
@@ -1297,6 +1302,10 @@ void orc_clover_EQ(const double* U, const int* dims, double* E_out, double* Q_ou
  * + O(a^6)].  The combination sum_m c_m q_m / m^4 over m = 1, 2, 3 with
  *   sum c_m = 1,  sum c_m m^2 = 0,  sum c_m m^4 = 0
  * removes the O(a^2) and O(a^4) terms at tree level: c = (3/2, -3/5, 1/10).
+ * Pinned by: the exact m x m charges of a constant abelian flux, the L^-8
+ * approach of the improved charge to the integer on it, the O(a^6) accuracy
+ * of the improved density on a smooth field, gauge invariance
+ * (tests/test_oracle_topo.py).
  */
 static const double IMPROVED_C[3] = {1.5, -0.6, 0.1};
 
@@ -1383,7 +1392,9 @@ void orc_topo_charge_improved(const double* U, const int* dims, double* out)
  * Wilson flow from t = 0 to t_end in steps of eps, a step that would pass the
  * next measurement time (or t_end) being shortened to end on it; E (clover)
  * and Q (charge 0: clover, 1: three-loop improved) at the ascending times
- * t_meas[0..n_meas-1] in [0, t_end].
+ * t_meas[0..n_meas-1] in [0, t_end].  Pinned by: on the step grid it equals
+ * the fixed-step flow bit for bit; shortened steps keep third-order
+ * convergence (tests/test_oracle_flow.py).
  */
 void orc_wilson_flow_times(double* W, const int* dims, double t_end, double eps, const double* t_meas, int n_meas,
                            int charge, double* E_out, double* Q_out)

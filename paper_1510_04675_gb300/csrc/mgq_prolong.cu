@@ -251,7 +251,9 @@ __device__ __forceinline__ void plaq_of(const Geom& gc, int d, int t, int& mu, i
 // (phase 0, d >= 1): the bonds of the previous stage (chi_mu = d) are copied
 // from cur to 1 - cur, so that both buffers agree outside the new stage's bonds.
 template <class T, int NP>
-__global__ void __launch_bounds__(PB_THREADS) k_ape_pb(const __grid_constant__ PBatch<T> B) {
+__global__ void __launch_bounds__(PB_THREADS, sizeof(T) == 8 ? 1 : 4) k_ape_pb(const __grid_constant__ PBatch<T> B) {
+    pdl_launch_dependents();
+    pdl_wait();  // the state and the fields come from the previous launch
     const int l = find_block(B.aprefix, B.n, blockIdx.x);
     const ProDesc<T>& D = B.d[l];
     const ProlongCtl* C = B.ctl + l;
@@ -320,6 +322,8 @@ __device__ __forceinline__ T plaq_retr(const Links<T, NP>& U, int mu, int nu, in
 // (Eq. smoothing) of the lattice's newest field, and the state update.
 template <class T, int NP>
 __global__ void __launch_bounds__(PB_SD_THREADS) k_sd_pb(const __grid_constant__ PBatch<T> B) {
+    pdl_launch_dependents();
+    pdl_wait();
     const int l = find_block(B.sprefix, B.n, blockIdx.x);
     const ProDesc<T>& D = B.d[l];
     ProlongCtl* C = B.ctl + l;
@@ -399,12 +403,12 @@ __global__ void __launch_bounds__(PB_THREADS) k_finish_pb(const __grid_constant_
 
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
-// partial-action blocks of one lattice: one block per 256 plaquettes of the
-// largest set (48 V_c = 3 V) for a lattice alone, up to PB_SD_MAXBLK; in a call
-// over many lattices the lattice's share of about 4096 blocks, so that the
-// blocks stay large when there is parallelism across lattices
+// partial-action blocks of one lattice: one block per 1024 plaquettes (four per
+// thread) of the largest set (48 V_c = 3 V) for a lattice alone, up to
+// PB_SD_MAXBLK; in a call over many lattices the lattice's share of about 4096
+// blocks, so that the blocks stay large when there is parallelism across lattices
 static int sd_blocks(const Geom& g, double total_sites) {
-    const long full = nblk(3L * g.V, PB_SD_THREADS);
+    const long full = nblk(3L * g.V, 4 * PB_SD_THREADS);
     long b = (long)((4096.0 * g.V + total_sites - 1.0) / total_sites);
     if (b > full) b = full;
     if (b > PB_SD_MAXBLK) b = PB_SD_MAXBLK;
@@ -485,8 +489,8 @@ static mgq_status prolong_run(const mgq_lattice* coarse, mgq_lattice* fine, void
     if ((s = cuda_check("prolongate: transfer"))) return s;
     auto iteration = [&]() {
         each_chunk([&]<class T, int NP>(const PBatch<T>& B, int) {
-            k_ape_pb<T, NP><<<B.aprefix[B.n], block_size(MGQ_KERNEL_APE, fine[0].prec), 0, st>>>(B);
-            k_sd_pb<T, NP><<<B.sprefix[B.n], PB_SD_THREADS, 0, st>>>(B);
+            launch_pdl(k_ape_pb<T, NP>, B.aprefix[B.n], block_size(MGQ_KERNEL_APE, fine[0].prec), st, B);
+            launch_pdl(k_sd_pb<T, NP>, B.sprefix[B.n], PB_SD_THREADS, st, B);
         });
     };
     if (budget > 0) {
