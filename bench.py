@@ -732,7 +732,9 @@ def run_mgq(args, dims, world, rank, local):
         "gpu_launches": K * (8 + 8 * n_or + 1),
         "ms_overrelax_sweep_with_plaquette": last_ms,
         "clocks": clocks,
-        "launch_shapes": {"threads_per_block": launch_shapes, "tuned_by": "paper_1510_04675_gb300.tune"},
+        "launch_shapes": {"threads_per_block": launch_shapes,
+                          "tuned_by": "fixed: staged FP32 12-real sub-sweeps" if args.prec == "f32c12"
+                          else "paper_1510_04675_gb300.tune"},
     }
     if clocks and clocks.get("sm_mhz"):
         # clock-normalised step: SM cycles per step at the median clock of the timed region

@@ -47,6 +47,22 @@ __device__ __forceinline__ const Geom& geom_of(const LatDesc<T>& d) {
     return d.g;
 }
 
+// The staple of U_MU(x) and the link itself: staged through shared memory for
+// FP32 12-real links (staple_staged; the launch gives STAGED_THREADS threads and
+// STAGED_SMEM bytes), as in the single-lattice kernels, so that batched and
+// single-lattice updates agree bit for bit; plain loads otherwise.
+template <class T, int NP, int MU>
+__device__ __forceinline__ void staple_and_link(const Links<T, NP>& U, const Geom& g, const int x[4], int h, int par,
+                                                M3<T>& A, M3<T>& u) {
+    if constexpr (sizeof(T) == 4 && NP == 6) {
+        extern __shared__ float4 staged_sm[];
+        A = staple_staged<MU>(U, g, x, h, par, staged_sm, u);
+    } else {
+        A = staple(U, g, x, h, MU, par);
+        u = U.load(MU, par, h);
+    }
+}
+
 // NHB1: single-attempt instance (the attempt loop is removed at compile time)
 template <class T, int NP, int MU, bool NHB1>
 __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4)
@@ -68,8 +84,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4)
     rk.idx_hi = idx_hi;
     int x[4];
     cb_coords(g, par, h, x);
-    const M3<T> A = staple(U, g, x, h, MU, par);
-    M3<T> u = U.load(MU, par, h);
+    M3<T> A, u;
+    staple_and_link<T, NP, MU>(U, g, x, h, par, A, u);
     hb_link(u, A, d.beta, n_hb, rk, (uint32_t)lex_of(g, x), (uint32_t)MU, (uint8_t*)nullptr);
     U.store(MU, par, h, u);
 }
@@ -88,8 +104,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4) k_overr
     U.S = d.g.S;
     int x[4];
     cb_coords(g, par, h, x);
-    const M3<T> A = staple(U, g, x, h, MU, par);
-    M3<T> u = U.load(MU, par, h);
+    M3<T> A, u;
+    staple_and_link<T, NP, MU>(U, g, x, h, par, A, u);
     or_link(u, A);
     U.store(MU, par, h, u);
 }
@@ -113,8 +129,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 8 ? 2 : 4)
         U.S = d.g.S;
         int x[4];
         cb_coords(g, par, h, x);
-        const M3<T> A = staple(U, g, x, h, 3, par);
-        M3<T> u = U.load(3, par, h);
+        M3<T> A, u;
+        staple_and_link<T, NP, 3>(U, g, x, h, par, A, u);
         if (par == 1) acc = (double)retr_nn(u, A);
         or_link(u, A);
         U.store(3, par, h, u);
@@ -240,8 +256,10 @@ mgq_status mgq_update_sweeps_batched(mgq_lattice* lats, int n_lat, const double*
         for (int first = 0; first < n_lat; first += BATCH_CHUNK) {
             const int n = (n_lat - first < BATCH_CHUNK) ? n_lat - first : BATCH_CHUNK;
             dispatch_prec(lats[0].prec, [&]<class T, int NP>() {
-                const int bh = block_size(MGQ_KERNEL_HEATBATH_BATCHED, lats[0].prec);
-                const int bo = block_size(MGQ_KERNEL_OVERRELAX_BATCHED, lats[0].prec);
+                const bool staged = sizeof(T) == 4 && NP == 6;
+                const int bh = staged ? STAGED_THREADS : block_size(MGQ_KERNEL_HEATBATH_BATCHED, lats[0].prec);
+                const int bo = staged ? STAGED_THREADS : block_size(MGQ_KERNEL_OVERRELAX_BATCHED, lats[0].prec);
+                const size_t smem = staged ? (size_t)STAGED_SMEM : 0;
                 Batch<T> Bl, Bo;
                 fill_batch(Bl, lats, betas, first, n, bh, true);
                 fill_batch(Bo, lats, betas, first, n, bo, true);
@@ -250,10 +268,10 @@ mgq_status mgq_update_sweeps_batched(mgq_lattice* lats, int n_lat, const double*
                     for (int par = 0; par < 2; par++)
                         dispatch_mu(mu, [&]<int MU>() {
                             if (n_hb == 1)
-                                launch_pdl(k_heatbath_batched<T, NP, MU, true>, nblocks, bh, st, Bl, par,
+                                launch_pdl_smem(k_heatbath_batched<T, NP, MU, true>, nblocks, bh, smem, st, Bl, par,
                                            (uint32_t)(sweep & 0xffffffffu), (uint32_t)(sweep >> 32), n_hb);
                             else
-                                launch_pdl(k_heatbath_batched<T, NP, MU, false>, nblocks, bh, st, Bl, par,
+                                launch_pdl_smem(k_heatbath_batched<T, NP, MU, false>, nblocks, bh, smem, st, Bl, par,
                                            (uint32_t)(sweep & 0xffffffffu), (uint32_t)(sweep >> 32), n_hb);
                         });
                 // with a plaquette record, the last overrelaxation sweep's
@@ -263,11 +281,11 @@ mgq_status mgq_update_sweeps_batched(mgq_lattice* lats, int n_lat, const double*
                     for (int mu = 0; mu < 4; mu++)
                         for (int par = 0; par < 2; par++) {
                             if (fold && k == n_or - 1 && mu == 3) {
-                                launch_pdl(k_overrelax_batched_last<T, NP>, oblocks, bo, st, Bo, par, partials);
+                                launch_pdl_smem(k_overrelax_batched_last<T, NP>, oblocks, bo, smem, st, Bo, par, partials);
                                 continue;
                             }
                             dispatch_mu(mu, [&]<int MU>() {
-                                launch_pdl(k_overrelax_batched<T, NP, MU>, oblocks, bo, st, Bo, par);
+                                launch_pdl_smem(k_overrelax_batched<T, NP, MU>, oblocks, bo, smem, st, Bo, par);
                             });
                         }
                 if (fold)

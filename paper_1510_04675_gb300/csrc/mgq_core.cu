@@ -262,6 +262,62 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4) k_overrelax(Links
     U.store(MU, par, h, u);
 }
 
+// FP32 12-real instances with the staple's links staged through shared memory
+// (staple_staged): the loads of each half-term are in flight during the
+// previous one's arithmetic; STAGED_THREADS threads per block (the tuned block
+// size does not apply), STAGED_SMEM bytes of dynamic shared memory.
+template <int MU>
+__global__ void __launch_bounds__(STAGED_THREADS, 4) k_heatbath_staged(Links<float, 6> U, Geom g, int par, float beta, RngKey rk) {
+    extern __shared__ float4 sm[];
+    pdl_launch_dependents();
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    int x[4];
+    cb_coords(g, par, h, x);
+    pdl_wait();
+    if (h >= g.Vh) return;
+    M3<float> u;
+    const M3<float> A = staple_staged<MU>(U, g, x, h, par, sm, u);
+    hb_link(u, A, beta, 1, rk, (uint32_t)lex_of(g, x), (uint32_t)MU, nullptr);
+    U.store(MU, par, h, u);
+}
+
+template <int MU>
+__global__ void __launch_bounds__(STAGED_THREADS, 4) k_overrelax_staged(Links<float, 6> U, Geom g, int par) {
+    extern __shared__ float4 sm[];
+    pdl_launch_dependents();
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    int x[4];
+    cb_coords(g, par, h, x);
+    pdl_wait();
+    if (h >= g.Vh) return;
+    M3<float> u;
+    const M3<float> A = staple_staged<MU>(U, g, x, h, par, sm, u);
+    or_link(u, A);
+    U.store(MU, par, h, u);
+}
+
+__global__ void __launch_bounds__(STAGED_THREADS, 4)
+    k_overrelax_last_staged(Links<float, 6> U, Geom g, int par, double* __restrict__ partials) {
+    extern __shared__ float4 sm[];
+    pdl_launch_dependents();
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    int x[4];
+    cb_coords(g, par, h, x);
+    pdl_wait();
+    if (h < g.Vh) {
+        M3<float> u;
+        const M3<float> A = staple_staged<3>(U, g, x, h, par, sm, u);
+        if (par == 1) acc = (double)retr_nn(u, A);
+        or_link(u, A);
+        U.store(3, par, h, u);
+        acc += site_plaquettes<float, 6, 3>(U, g, par, h);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+
 // The two sub-sweeps of direction 3, which end an overrelaxation sweep, with
 // the plaquette of the field they leave folded in (per-block FP64 partials).
 // Neither sub-sweep writes directions 0-2, so each adds the plaquettes of the
@@ -365,6 +421,13 @@ mgq_status heatbath_subsweep(mgq_lattice* lat, double beta, uint64_t sweep, int 
     const RngKey rk = make_rng(lat->seed, lat->lattice_id, sweep);
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
         dispatch_mu(mu, [&]<int MU>() {
+            if constexpr (sizeof(T) == 4 && NP == 6) {
+                if (n_hb == 1 && !dec) {
+                    launch_pdl_smem(k_heatbath_staged<MU>, nblk(g.Vh, STAGED_THREADS), STAGED_THREADS, STAGED_SMEM, st,
+                                    links_of<T, NP>(lat), g, par, (float)beta, rk);
+                    return;
+                }
+            }
             if (n_hb == 1 && !dec)
                 launch_pdl(k_heatbath<T, NP, MU, true>, nblk(g.Vh, bs), bs, st, links_of<T, NP>(lat), g, par,
                            (T)beta, rk, n_hb, dec);
@@ -382,7 +445,11 @@ mgq_status overrelax_subsweep(mgq_lattice* lat, int mu, int par, cudaStream_t st
     const int bs = g_block[MGQ_KERNEL_OVERRELAX][lat->prec];
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
         dispatch_mu(mu, [&]<int MU>() {
-            launch_pdl(k_overrelax<T, NP, MU>, nblk(g.Vh, bs), bs, st, links_of<T, NP>(lat), g, par);
+            if constexpr (sizeof(T) == 4 && NP == 6)
+                launch_pdl_smem(k_overrelax_staged<MU>, nblk(g.Vh, STAGED_THREADS), STAGED_THREADS, STAGED_SMEM, st,
+                                links_of<T, NP>(lat), g, par);
+            else
+                launch_pdl(k_overrelax<T, NP, MU>, nblk(g.Vh, bs), bs, st, links_of<T, NP>(lat), g, par);
         });
     });
     return cuda_check("mgq_overrelax");
@@ -397,12 +464,17 @@ mgq_status overrelax_sweep_plaquette(mgq_lattice* lat, double* dev_out, cudaStre
             if ((s = overrelax_subsweep(lat, mu, par, st))) return s;
     Trace trace("overrelax_last");
     const Geom g = make_geom(lat->dims);
-    const int bs = g_block[MGQ_KERNEL_OVERRELAX][lat->prec];
+    const int bs = lat->prec == MGQ_F32_C12 ? STAGED_THREADS : g_block[MGQ_KERNEL_OVERRELAX][lat->prec];
     const int nb = nblk(g.Vh, bs);
     double* partials = reinterpret_cast<double*>(ws_alg(lat));  // free during sweeps; >= 2 nb doubles
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
-        for (int par = 0; par < 2; par++)
-            launch_pdl(k_overrelax_last<T, NP>, nb, bs, st, links_of<T, NP>(lat), g, par, partials + par * nb);
+        for (int par = 0; par < 2; par++) {
+            if constexpr (sizeof(T) == 4 && NP == 6)
+                launch_pdl_smem(k_overrelax_last_staged, nb, STAGED_THREADS, STAGED_SMEM, st,
+                                links_of<T, NP>(lat), g, par, partials + par * nb);
+            else
+                launch_pdl(k_overrelax_last<T, NP>, nb, bs, st, links_of<T, NP>(lat), g, par, partials + par * nb);
+        }
     });
     launch_final_sum(partials, 2 * nb, 1.0 / (18.0 * (double)g.V), dev_out, st);
     return cuda_check("overrelax_sweep_plaquette");

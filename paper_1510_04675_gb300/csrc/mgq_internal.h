@@ -95,6 +95,22 @@ inline void launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream
     cudaLaunchKernelEx(&cfg, kernel, (KArgs)args...);
 }
 
+// launch with programmatic stream serialisation and dynamic shared memory
+template <class... KArgs, class... Args>
+inline void launch_pdl_smem(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, (KArgs)args...);
+}
+
 
 template <class T, int NP>
 inline Links<T, NP> links_of(const mgq_lattice* lat) {

@@ -95,6 +95,120 @@ __device__ __forceinline__ M3<T> staple_two_row(const LinkField& U, const Geom& 
     return A;
 }
 
+// ---- the two-row staple with its links staged through shared memory ----
+// For FP32 12-real (paired) links.  The staple's six half-terms (the up and the
+// down product of each direction nu != mu, in increasing nu) each need three
+// links; the thread copies the links of half-term k+1 into its own
+// shared-memory slots with cp.async while it computes half-term k from the
+// other buffer, so those loads are in flight during the arithmetic without
+// holding registers.  The updated link itself is staged with the first
+// half-term and read back after the staple.  Each half-term is added to A as
+// it completes (A += up, A += dn).  sm: (2 stages x 3 links + 1) x 3 pair-planes
+// x STAGED_THREADS float4 (STAGED_SMEM bytes per block of STAGED_THREADS
+// threads), each thread using its own column; the fixed block size keeps every
+// slot address a constant offset from one base.
+constexpr int STAGED_THREADS = 128;
+constexpr int STAGED_SMEM = (2 * 3 + 1) * 3 * 16 * STAGED_THREADS;
+
+__device__ __forceinline__ void cp_async16(float4* smem, const float4* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(__cvta_generic_to_global(gmem)) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// slot j of a stage (j = 0..2), or the updated link's slot (stage 2, j = 0)
+__device__ __forceinline__ float4* staged_slot(float4* sm, int stage, int j, int k) {
+    return sm + ((stage * 3 + j) * 3 + k) * STAGED_THREADS + threadIdx.x;
+}
+__device__ __forceinline__ void stage_link(float4* sm, int stage, int j, const Links<float, 6>& U, int mu, int par, int h) {
+    const float4* q = reinterpret_cast<const float4*>(U.block(mu, par, h)) + (h & 31);
+#pragma unroll
+    for (int k = 0; k < 3; k++) cp_async16(staged_slot(sm, stage, j, k), q + (k << 5));
+}
+__device__ __forceinline__ M3<float> staged_rows(float4* sm, int stage, int j) {
+    M3<float> m;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float4 v = *staged_slot(sm, stage, j, k);
+        m.e[(2 * k) / 3][(2 * k) % 3] = mk(v.x, v.y);
+        m.e[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(v.z, v.w);
+    }
+    return m;
+}
+__device__ __forceinline__ M3<float> staged_full(float4* sm, int stage, int j) {
+    M3<float> m = staged_rows(sm, stage, j);
+    rebuild_row2(m);
+    return m;
+}
+
+// A = the staple of U_MU(x) (as staple_two_row, with the accumulation above);
+// u = U_MU(x) (full, row 2 rebuilt).
+template <int MU>
+__device__ __forceinline__ M3<float> staple_staged(const Links<float, 6>& U, const Geom& g, const int x[4], int h,
+                                                   int par, float4* sm, M3<float>& u) {
+    const int op = par ^ 1;
+    const Hops H = make_hops(g, x);
+    const int fmu = pick(H.fwd, MU);
+    const int hpm = (H.lex + fmu) >> 1;
+    int hpn[3], hmn[3], hpm_mn[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const int nu = i < MU ? i : i + 1;
+        hpn[i] = (H.lex + pick(H.fwd, nu)) >> 1;
+        hmn[i] = (H.lex + pick(H.bwd, nu)) >> 1;
+        hpm_mn[i] = (H.lex + fmu + pick(H.bwd, nu)) >> 1;
+    }
+    // half-term k: nu = the (k/2)-th direction other than MU; even k: up = (a b^+) c^+
+    // with a = U_nu(x+mu), b = U_mu(x+nu), c = U_nu(x); odd k: dn = (e d)^+ f with
+    // d = U_nu(x+mu-nu), e = U_mu(x-nu), f = U_nu(x-nu)
+    auto issue = [&](int k, int stage) {
+        const int i = k >> 1, nu = i < MU ? i : i + 1;
+        if ((k & 1) == 0) {
+            stage_link(sm, stage, 0, U, nu, op, hpm);
+            stage_link(sm, stage, 1, U, MU, op, hpn[i]);
+            stage_link(sm, stage, 2, U, nu, par, h);
+        } else {
+            stage_link(sm, stage, 0, U, nu, par, hpm_mn[i]);
+            stage_link(sm, stage, 1, U, MU, op, hmn[i]);
+            stage_link(sm, stage, 2, U, nu, op, hmn[i]);
+        }
+    };
+    stage_link(sm, 2, 0, U, MU, par, h);  // the updated link, with the first half-term
+    issue(0, 0);
+    cp_async_commit();
+    issue(1, 1);
+    cp_async_commit();
+    M3<float> A;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) A.e[i][j] = mk(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        if (k < 5) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        const int st = k & 1;
+        M3<float> term;
+        if ((k & 1) == 0) {
+            const M3<float> t = mul_nd_2(staged_rows(sm, st, 0), staged_full(sm, st, 1));
+            term = mul_nd_2(t, staged_full(sm, st, 2));
+        } else {
+            M3<float> t = mul_nn_2(staged_rows(sm, st, 1), staged_full(sm, st, 0));
+            rebuild_row2(t);
+            term = mul_dn_2(t, staged_full(sm, st, 2));
+        }
+        rebuild_row2(term);
+        acc_add(A, term);
+        if (k + 2 < 6) {
+            issue(k + 2, st);
+            cp_async_commit();
+        }
+    }
+    u = staged_full(sm, 2, 0);
+    return A;
+}
+
 // Full products in the oracle's order (the FP64 parity path).
 template <class T, int NP>
 __device__ __forceinline__ M3<T> staple_full(const Links<T, NP>& U, const Geom& g, const int x[4], int h, int mu,

@@ -20,6 +20,7 @@ from . import _lib, api
 from ._lib import MGQ_KERNEL_HEATBATH, MGQ_KERNEL_OVERRELAX, call
 
 CANDIDATES = (32, 64, 96, 128)
+STAGED_THREADS = 128  # block size of the FP32 12-real sub-sweeps (not tunable)
 _KERNELS = {"heatbath": MGQ_KERNEL_HEATBATH, "overrelax": MGQ_KERNEL_OVERRELAX, "heatbath_batched": 2,
             "overrelax_batched": 3, "ape": 4}
 
@@ -56,7 +57,11 @@ def _time(fn, reps: int) -> float:
 def autotune(lat: "api.Lattice", beta: float = 6.0, candidates: Sequence[int] = CANDIDATES, reps: int = 5,
              cache_path: Optional[str] = None, use_cache: bool = True) -> Dict[str, int]:
     """Choose and install the fastest block size per kernel for this lattice's
-    extents and format; returns {"heatbath": threads, "overrelax": threads}."""
+    extents and format; returns {"heatbath": threads, "overrelax": threads}.
+    FP32 12-real sub-sweeps stage their staple links through shared memory at a
+    fixed 128 threads per block, so there is nothing to tune for that format."""
+    if lat.prec == "f32c12":
+        return {"heatbath": STAGED_THREADS, "overrelax": STAGED_THREADS}
     path = cache_path or default_cache_path()
     key = _key(lat)
     cache = {}
@@ -120,6 +125,8 @@ def autotune_batched(batch: "api.Batch", candidates: Sequence[int] = CANDIDATES,
     overrelaxation), then the overrelaxation inside compound sweeps (1 HB + 4 OR)
     with the chosen heat-bath size.  The batch's links are advanced by the timing."""
     prec = batch.lattices[0].prec
+    if prec == "f32c12":  # staged sub-sweeps, a fixed 128 threads per block
+        return {"heatbath_batched": STAGED_THREADS, "overrelax_batched": STAGED_THREADS}
     shapes = sorted({"x".join(map(str, l.dims)) for l in batch.lattices})
     key = f"{torch.cuda.get_device_name(batch.lattices[0].device)}|batched|{batch.n}|{','.join(shapes)}|{prec}"
 
