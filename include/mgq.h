@@ -108,10 +108,10 @@ uint64_t mgq_workspace_bytes(const mgq_lattice* lat);
  * (heat bath and overrelaxation) of the single-lattice and the batched entry
  * points and of the APE step of the prolongation: 32, 64, 96 or 128 (the
  * kernels are compiled for at most 128); 128 by default.  Results do not
- * depend on it (one thread per link or per active bond).  The FP32 12-real
- * sub-sweeps (single and batched) stage their staple links through shared
- * memory and always run 128 threads per block; the setting applies to the other
- * formats.  The force kernel's shape is structural (eight warps cover the
+ * depend on it (one thread per link or per active bond).  FP32 12-real
+ * sub-sweeps of the batched driver, and of single lattices with V/2 >= 49152,
+ * stage their staple links through shared memory and always run 128 threads
+ * per block; the setting applies to the other launches.  The force kernel's shape is structural (eight warps cover the
  * eight (mu, parity) planes of a 32-site band) and not tuned.  Process-wide setting; change it only while no
  * call is being issued.  Set by the autotuner (paper_1510_04675_gb300/tune.py). */
 typedef enum {

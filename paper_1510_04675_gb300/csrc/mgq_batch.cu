@@ -56,7 +56,7 @@ __device__ __forceinline__ void staple_and_link(const Links<T, NP>& U, const Geo
                                                 M3<T>& A, M3<T>& u) {
     if constexpr (sizeof(T) == 4 && NP == 6) {
         extern __shared__ float4 staged_sm[];
-        A = staple_staged<MU>(U, g, x, h, par, staged_sm, u);
+        A = staple_staged(U, g, x, h, MU, par, staged_sm, u);
     } else {
         A = staple(U, g, x, h, MU, par);
         u = U.load(MU, par, h);

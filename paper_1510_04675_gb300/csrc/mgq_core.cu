@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4) k_overrelax(Links
 // previous one's arithmetic; STAGED_THREADS threads per block (the tuned block
 // size does not apply), STAGED_SMEM bytes of dynamic shared memory.
 template <int MU>
-__global__ void __launch_bounds__(STAGED_THREADS, 4) k_heatbath_staged(Links<float, 6> U, Geom g, int par, float beta, RngKey rk) {
+__global__ void __launch_bounds__(STAGED_THREADS, 5) k_heatbath_staged(Links<float, 6> U, Geom g, int par, float beta, RngKey rk) {
     extern __shared__ float4 sm[];
     pdl_launch_dependents();
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
@@ -276,13 +276,19 @@ __global__ void __launch_bounds__(STAGED_THREADS, 4) k_heatbath_staged(Links<flo
     pdl_wait();
     if (h >= g.Vh) return;
     M3<float> u;
-    const M3<float> A = staple_staged<MU>(U, g, x, h, par, sm, u);
-    hb_link(u, A, beta, 1, rk, (uint32_t)lex_of(g, x), (uint32_t)MU, nullptr);
+    uint4 r[3];
+    const uint32_t lex = (uint32_t)lex_of(g, x);
+    // the three Philox draws while the first staged loads are in flight
+    const M3<float> A = staple_staged(U, g, x, h, MU, par, sm, u, [&]() {
+#pragma unroll
+        for (int s = 0; s < 3; s++) r[s] = draw(rk, lex, (uint32_t)MU, (uint32_t)s, 0u, KIND_HB);
+    });
+    hb_link_drawn(u, A, beta, r);
     U.store(MU, par, h, u);
 }
 
 template <int MU>
-__global__ void __launch_bounds__(STAGED_THREADS, 4) k_overrelax_staged(Links<float, 6> U, Geom g, int par) {
+__global__ void __launch_bounds__(STAGED_THREADS, 5) k_overrelax_staged(Links<float, 6> U, Geom g, int par) {
     extern __shared__ float4 sm[];
     pdl_launch_dependents();
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
@@ -291,7 +297,7 @@ __global__ void __launch_bounds__(STAGED_THREADS, 4) k_overrelax_staged(Links<fl
     pdl_wait();
     if (h >= g.Vh) return;
     M3<float> u;
-    const M3<float> A = staple_staged<MU>(U, g, x, h, par, sm, u);
+    const M3<float> A = staple_staged(U, g, x, h, MU, par, sm, u);
     or_link(u, A);
     U.store(MU, par, h, u);
 }
@@ -307,7 +313,7 @@ __global__ void __launch_bounds__(STAGED_THREADS, 4)
     pdl_wait();
     if (h < g.Vh) {
         M3<float> u;
-        const M3<float> A = staple_staged<3>(U, g, x, h, par, sm, u);
+        const M3<float> A = staple_staged(U, g, x, h, 3, par, sm, u);
         if (par == 1) acc = (double)retr_nn(u, A);
         or_link(u, A);
         U.store(3, par, h, u);
@@ -422,7 +428,7 @@ mgq_status heatbath_subsweep(mgq_lattice* lat, double beta, uint64_t sweep, int 
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
         dispatch_mu(mu, [&]<int MU>() {
             if constexpr (sizeof(T) == 4 && NP == 6) {
-                if (n_hb == 1 && !dec) {
+                if (n_hb == 1 && !dec && g.Vh >= STAGED_MIN_VH) {
                     launch_pdl_smem(k_heatbath_staged<MU>, nblk(g.Vh, STAGED_THREADS), STAGED_THREADS, STAGED_SMEM, st,
                                     links_of<T, NP>(lat), g, par, (float)beta, rk);
                     return;
@@ -445,9 +451,9 @@ mgq_status overrelax_subsweep(mgq_lattice* lat, int mu, int par, cudaStream_t st
     const int bs = g_block[MGQ_KERNEL_OVERRELAX][lat->prec];
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
         dispatch_mu(mu, [&]<int MU>() {
-            if constexpr (sizeof(T) == 4 && NP == 6)
+            if (sizeof(T) == 4 && NP == 6 && g.Vh >= STAGED_MIN_VH)
                 launch_pdl_smem(k_overrelax_staged<MU>, nblk(g.Vh, STAGED_THREADS), STAGED_THREADS, STAGED_SMEM, st,
-                                links_of<T, NP>(lat), g, par);
+                                links_of<float, 6>(lat), g, par);
             else
                 launch_pdl(k_overrelax<T, NP, MU>, nblk(g.Vh, bs), bs, st, links_of<T, NP>(lat), g, par);
         });
@@ -464,14 +470,15 @@ mgq_status overrelax_sweep_plaquette(mgq_lattice* lat, double* dev_out, cudaStre
             if ((s = overrelax_subsweep(lat, mu, par, st))) return s;
     Trace trace("overrelax_last");
     const Geom g = make_geom(lat->dims);
-    const int bs = lat->prec == MGQ_F32_C12 ? STAGED_THREADS : g_block[MGQ_KERNEL_OVERRELAX][lat->prec];
+    const bool staged = lat->prec == MGQ_F32_C12 && g.Vh >= STAGED_MIN_VH;
+    const int bs = staged ? STAGED_THREADS : g_block[MGQ_KERNEL_OVERRELAX][lat->prec];
     const int nb = nblk(g.Vh, bs);
     double* partials = reinterpret_cast<double*>(ws_alg(lat));  // free during sweeps; >= 2 nb doubles
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
         for (int par = 0; par < 2; par++) {
-            if constexpr (sizeof(T) == 4 && NP == 6)
+            if (staged)
                 launch_pdl_smem(k_overrelax_last_staged, nb, STAGED_THREADS, STAGED_SMEM, st,
-                                links_of<T, NP>(lat), g, par, partials + par * nb);
+                                links_of<float, 6>(lat), g, par, partials + par * nb);
             else
                 launch_pdl(k_overrelax_last<T, NP>, nb, bs, st, links_of<T, NP>(lat), g, par, partials + par * nb);
         }

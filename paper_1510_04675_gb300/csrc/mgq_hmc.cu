@@ -37,6 +37,34 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_force(Links<T, 
     }
 }
 
+// FP32 12-real force with the staple's links staged through shared memory
+// (staple_staged): a block of 4 warps covers the 4 directions of one parity for
+// a 32-site band (block b: band b/2, parity b%2).
+__global__ void __launch_bounds__(STAGED_THREADS, 5) k_force_staged(Links<float, 6> U, Geom g, Alg<float> B, float coef,
+                                                                  float alpha) {
+    extern __shared__ float4 sm[];
+    pdl_launch_dependents();
+    const int mu = threadIdx.x >> 5, par = blockIdx.x & 1;
+    const int h = (blockIdx.x >> 1) * 32 + (threadIdx.x & 31);
+    int x[4];
+    cb_coords(g, par, h, x);
+    pdl_wait();
+    if (h >= g.Vh) return;
+    M3<float> u;
+    const M3<float> A = staple_staged(U, g, x, h, mu, par, sm, u);
+    const M3<float> M = mul_nn(u, A);
+    float t[8];
+    ta_coeffs(M, t);
+    float* b = B.at(mu, par, h);
+    if (alpha == 0.f) {
+#pragma unroll
+        for (int a = 0; a < 8; a++) b[a * Alg<float>::kStep] = coef * t[a];
+    } else {
+#pragma unroll
+        for (int a = 0; a < 8; a++) b[a * Alg<float>::kStep] = alpha * b[a * Alg<float>::kStep] + coef * t[a];
+    }
+}
+
 // U <- exp(s B) U on every link; the FP32 formats are reunitarised.
 template <class T, int NP>
 __global__ void __launch_bounds__(128) k_exp_update(Links<T, NP> U, Geom g, Alg<T> B, T s) {
@@ -133,8 +161,12 @@ static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 mgq_status force_accumulate(const mgq_lattice* lat, void* B, double coef, double alpha, cudaStream_t st) {
     const Geom g = make_geom(lat->dims);
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
-        launch_pdl(k_force<T, NP>, nblk(g.Vh, 32), 256, st, links_of<T, NP>(lat), g, alg_at<T>(B, lat->dims),
-                   (T)coef, (T)alpha);
+        if constexpr (sizeof(T) == 4 && NP == 6)
+            launch_pdl_smem(k_force_staged, 2 * nblk(g.Vh, 32), STAGED_THREADS, STAGED_SMEM, st, links_of<T, NP>(lat), g,
+                            alg_at<T>(B, lat->dims), (T)coef, (T)alpha);
+        else
+            launch_pdl(k_force<T, NP>, nblk(g.Vh, 32), 256, st, links_of<T, NP>(lat), g, alg_at<T>(B, lat->dims),
+                       (T)coef, (T)alpha);
     });
     return cuda_check("force");
 }

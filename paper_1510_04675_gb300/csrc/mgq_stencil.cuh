@@ -52,7 +52,9 @@ template <> __device__ __forceinline__ M3<float> mul_dn_2<float>(const M3<float>
 // so that Re Tr(U_mu(x) A_mu(x)) sums the six plaquettes holding U_mu(x).
 // x has parity par; x +- e_nu has parity 1 - par, x + e_mu - e_nu parity par.
 //
-// Staple in two-row form (FP32 links, 12- or 18-real).  Each staple term is a product of three
+// Staple in two-row form (FP32 links, 12- or 18-real); each half-term is added to A
+// as it completes (A += up, A += dn), the order of staple_staged, so that staged and
+// unstaged kernels agree bit for bit.  Each staple term is a product of three
 // SU(3) links, hence in SU(3): only rows 0, 1 of every partial product are
 // computed and row 2 is rebuilt, and a link that enters only through its rows
 // (the left factor) is never completed.
@@ -89,8 +91,8 @@ __device__ __forceinline__ M3<T> staple_two_row(const LinkField& U, const Geom& 
             dn = mul_dn_2(t, U.load(nu, op, hmn));
             rebuild_row2(dn);
         }
-        acc_add(up, dn);
         acc_add(A, up);
+        acc_add(A, dn);
     }
     return A;
 }
@@ -106,8 +108,11 @@ __device__ __forceinline__ M3<T> staple_two_row(const LinkField& U, const Geom& 
 // it completes (A += up, A += dn).  sm: (2 stages x 3 links + 1) x 3 pair-planes
 // x STAGED_THREADS float4 (STAGED_SMEM bytes per block of STAGED_THREADS
 // threads), each thread using its own column; the fixed block size keeps every
-// slot address a constant offset from one base.
+// slot address a constant offset from one base.  Single-lattice sub-sweeps use
+// it from STAGED_MIN_VH links per launch on: below about a wave of blocks the
+// serial half-term pipeline of each thread is not hidden by other warps.
 constexpr int STAGED_THREADS = 128;
+constexpr int STAGED_MIN_VH = 49152;
 constexpr int STAGED_SMEM = (2 * 3 + 1) * 3 * 16 * STAGED_THREADS;
 
 __device__ __forceinline__ void cp_async16(float4* smem, const float4* gmem) {
@@ -143,10 +148,16 @@ __device__ __forceinline__ M3<float> staged_full(float4* sm, int stage, int j) {
 }
 
 // A = the staple of U_MU(x) (as staple_two_row, with the accumulation above);
-// u = U_MU(x) (full, row 2 rebuilt).
-template <int MU>
+// u = U_MU(x) (full, row 2 rebuilt).  MU may be a run-time direction (the
+// force kernel's warps); the sub-sweeps pass a compile-time one.
+struct NoWork {
+    __device__ void operator()() const {}
+};
+// early(): independent work that runs while the first loads are in flight.
+template <class Work = NoWork>
 __device__ __forceinline__ M3<float> staple_staged(const Links<float, 6>& U, const Geom& g, const int x[4], int h,
-                                                   int par, float4* sm, M3<float>& u) {
+                                                   const int MU, int par, float4* sm, M3<float>& u,
+                                                   Work early = Work()) {
     const int op = par ^ 1;
     const Hops H = make_hops(g, x);
     const int fmu = pick(H.fwd, MU);
@@ -179,6 +190,7 @@ __device__ __forceinline__ M3<float> staple_staged(const Links<float, 6>& U, con
     cp_async_commit();
     issue(1, 1);
     cp_async_commit();
+    early();
     M3<float> A;
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -431,6 +443,29 @@ __device__ __forceinline__ void creutz_phi(float u3, float* s, float* c) {
 //   a0 = 1 + log1p((1 - u0) expm1(-2k)) / k, accept iff u1^2 <= 1 - a0^2,
 // direction cos(theta) = 2 u2 - 1, phi = 2 pi u3; R = X (w/|w|), U <- R U,
 // V <- R V; reunitarise at the end.  dec[s] = accepted attempt or 255.
+
+// One Creutz attempt on subgroup s with the four words r; on acceptance
+// applies R = X (w/|w|) to u and v and returns true.
+template <class T>
+__device__ __forceinline__ bool creutz_attempt(M3<T>& u, M3<T>& v, int s, const T w[4], T xi, T k, T em, uint4 r) {
+    const T u0 = u01<T>(r.x), u1 = u01<T>(r.y), u2 = u01<T>(r.z), u3 = u01<T>(r.w);
+    const T a0 = creutz_a0(k, em, u0);
+    const T rest = sub_rn(T(1), mul_rn(a0, a0));
+    if (!(mul_rn(u1, u1) <= rest)) return false;
+    const T rad = sampler_sqrt(rest);
+    const T ct = T(2) * u2 - T(1);
+    const T st = sampler_sqrt(sub_rn(T(1), mul_rn(ct, ct)));
+    T sp, cp;
+    creutz_phi(u3, &sp, &cp);
+    const T X[4] = {a0, rad * st * cp, rad * st * sp, rad * ct};
+    const T inv = recip(xi);
+    const T wh[4] = {w[0] * inv, w[1] * inv, w[2] * inv, w[3] * inv};
+    T R[4];
+    qmul(X, wh, R);
+    apply_subgroup(u, v, s, R);
+    return true;
+}
+
 template <class T>
 __device__ __forceinline__ void hb_link(M3<T>& u, const M3<T>& A, T beta, int n_hb, const RngKey& rk, uint32_t lex,
                                         uint32_t mu, uint8_t* dec) {
@@ -446,28 +481,32 @@ __device__ __forceinline__ void hb_link(M3<T>& u, const M3<T>& A, T beta, int n_
             const T k = creutz_k(beta, xi);
             const T em = creutz_em(k);
             for (int att = 0; att < n_hb; att++) {
-                const uint4 r = draw(rk, lex, mu, (uint32_t)s, (uint32_t)att, KIND_HB);
-                const T u0 = u01<T>(r.x), u1 = u01<T>(r.y), u2 = u01<T>(r.z), u3 = u01<T>(r.w);
-                const T a0 = creutz_a0(k, em, u0);
-                const T rest = sub_rn(T(1), mul_rn(a0, a0));
-                if (mul_rn(u1, u1) <= rest) {
-                    const T rad = sampler_sqrt(rest);
-                    const T ct = T(2) * u2 - T(1);
-                    const T st = sampler_sqrt(sub_rn(T(1), mul_rn(ct, ct)));
-                    T sp, cp;
-                    creutz_phi(u3, &sp, &cp);
-                    const T X[4] = {a0, rad * st * cp, rad * st * sp, rad * ct};
-                    const T inv = recip(xi);
-                    const T wh[4] = {w[0] * inv, w[1] * inv, w[2] * inv, w[3] * inv};
-                    T R[4];
-                    qmul(X, wh, R);
-                    apply_subgroup(u, v, s, R);
+                if (creutz_attempt(u, v, s, w, xi, k, em, draw(rk, lex, mu, (uint32_t)s, (uint32_t)att, KIND_HB))) {
                     d = (uint8_t)att;
                     break;
                 }
             }
         }
         if (dec) dec[s] = d;
+    }
+    reunitarize(u);
+}
+
+// The single-attempt heat bath with the three draws given (r[s]: subgroup s,
+// attempt 0), so that a kernel can draw them while its loads are in flight.
+template <class T>
+__device__ __forceinline__ void hb_link_drawn(M3<T>& u, const M3<T>& A, T beta, const uint4 r[3]) {
+    M3<T> v = mul_nn(u, A);
+#pragma unroll
+    for (int s = 0; s < 3; s++) {
+        const int i = (s == 2) ? 1 : 0, j = (s == 0) ? 1 : 2;
+        T w[4];
+        block_w(v, i, j, w);
+        const T xi = m_sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+        if (xi >= tiny_norm<T>()) {
+            const T k = creutz_k(beta, xi);
+            creutz_attempt(u, v, s, w, xi, k, creutz_em(k), r[s]);
+        }
     }
     reunitarize(u);
 }

@@ -20,7 +20,8 @@ from . import _lib, api
 from ._lib import MGQ_KERNEL_HEATBATH, MGQ_KERNEL_OVERRELAX, call
 
 CANDIDATES = (32, 64, 96, 128)
-STAGED_THREADS = 128  # block size of the FP32 12-real sub-sweeps (not tunable)
+STAGED_THREADS = 128  # block size of the staged FP32 12-real sub-sweeps (not tunable)
+STAGED_MIN_VH = 49152  # single-lattice FP32 12-real sub-sweeps are staged from V/2 >= this on
 _KERNELS = {"heatbath": MGQ_KERNEL_HEATBATH, "overrelax": MGQ_KERNEL_OVERRELAX, "heatbath_batched": 2,
             "overrelax_batched": 3, "ape": 4}
 
@@ -58,10 +59,9 @@ def autotune(lat: "api.Lattice", beta: float = 6.0, candidates: Sequence[int] = 
              cache_path: Optional[str] = None, use_cache: bool = True) -> Dict[str, int]:
     """Choose and install the fastest block size per kernel for this lattice's
     extents and format; returns {"heatbath": threads, "overrelax": threads}.
-    FP32 12-real sub-sweeps stage their staple links through shared memory at a
-    fixed 128 threads per block, so there is nothing to tune for that format."""
-    if lat.prec == "f32c12":
-        return {"heatbath": STAGED_THREADS, "overrelax": STAGED_THREADS}
+    FP32 12-real sub-sweeps of lattices with V/2 >= STAGED_MIN_VH stage their
+    staple links through shared memory at a fixed 128 threads per block; for
+    them the candidates time alike and the choice has no effect."""
     path = cache_path or default_cache_path()
     key = _key(lat)
     cache = {}

@@ -11,11 +11,8 @@ pytestmark = pytest.mark.gpu
 def test_autotune_and_launch_shape_independence(gpu, tmp_path):
     from paper_1510_04675_gb300 import tune
 
-    # FP32 18-real: the 12-real sub-sweeps run staged at a fixed block size
     lat = gpu.Lattice([8, 8, 8, 8], "f32", seed=4)
     gpu.mgq_init_links(lat, 1)
-    c12 = gpu.Lattice([8, 8, 8, 8], "f32c12", seed=4)
-    assert tune.autotune(c12, cache_path=str(tmp_path / "none.json")) == {"heatbath": 128, "overrelax": 128}
     cache = str(tmp_path / "tune.json")
     choice = tune.autotune(lat, cache_path=cache)
     assert set(choice) == {"heatbath", "overrelax"}
