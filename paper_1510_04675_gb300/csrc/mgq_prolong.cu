@@ -2,6 +2,8 @@
 // transfer step of the prolongation (Eq. prolongation) and the interpolation
 // stages, each a repeated Jacobi APE step (Eq. APE) on the active bonds of
 // stage d that minimises the partial action S_d (Eq. smoothing).
+#include <vector>
+
 #include "mgq_internal.h"
 #include "mgq_stencil.cuh"
 
@@ -13,6 +15,8 @@ namespace mgq {
 // pass whose three rotations all round to the identity (|r - 1| below half an
 // FP32 unit in the last place of 1 in every component): later passes would
 // not move W by more than FP32 rounding.
+// FP32 also takes 1/|w| from the hardware reciprocal square root and updates
+// the two rows with packed FMAs (su2_rows).
 template <class T>
 __device__ __forceinline__ M3<T> su3_project(const M3<T>& M) {
     constexpr int NPASS = 8;
@@ -27,13 +31,20 @@ __device__ __forceinline__ M3<T> su3_project(const M3<T>& M) {
             const M3<T> V = mul_nd(W, M);
             T w[4];
             block_w(V, i, j, w);
-            const T xi = m_sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
-            if (!(xi >= tiny_norm<T>())) continue;
-            const T inv = T(1) / xi;
-            const T r[4] = {w[0] * inv, w[1] * inv, w[2] * inv, w[3] * inv};
-            if constexpr (sizeof(T) == 4)
+            const T n2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + w[3] * w[3];
+            if constexpr (sizeof(T) == 4) {
+                if (!(n2 >= 1e-30f)) continue;
+                const float inv = rsqrtf(n2);
+                const float r[4] = {w[0] * inv, w[1] * inv, w[2] * inv, w[3] * inv};
                 moved = moved || fabsf(r[1]) > 3e-8f || fabsf(r[2]) > 3e-8f || fabsf(r[3]) > 3e-8f;
-            left_su2(W, i, j, r);
+                su2_rows(W, i, j, r, true, true, 7, 7);
+            } else {
+                const T xi = m_sqrt(n2);
+                if (!(xi >= tiny_norm<T>())) continue;
+                const T inv = T(1) / xi;
+                const T r[4] = {w[0] * inv, w[1] * inv, w[2] * inv, w[3] * inv};
+                left_su2(W, i, j, r);
+            }
         }
         if constexpr (sizeof(T) == 4) {
             if (!moved) break;
@@ -279,9 +290,18 @@ __global__ void __launch_bounds__(PB_THREADS, sizeof(T) == 8 ? 1 : 4) k_ape_pb(c
         if (nu == mu || !(x[nu] & 1)) continue;
         const int lpn = lex_hop(g, x, nu, +1), lmn = lex_hop(g, x, nu, -1);
         const int lmn_pm = lex_hop(g, x, nu, -1, mu, +1);
-        const M3<T> tp = mul_nd(mul_nn(Uin.load(nu, par, h), Uin.load(mu, op, lpn >> 1)), Uin.load(nu, op, lpm >> 1));
-        const M3<T> tm = mul_nn(mul_dn(Uin.load(nu, op, lmn >> 1), Uin.load(mu, op, lmn >> 1)),
-                                Uin.load(nu, par, lmn_pm >> 1));
+        M3<T> tp, tm;
+        if constexpr (sizeof(T) == 4) {
+            // products of SU(3) factors in two-row form, the third row rebuilt
+            tp = mul_nd_2(mul_nn_2(Uin.load_rows(nu, par, h), Uin.load(mu, op, lpn >> 1)), Uin.load(nu, op, lpm >> 1));
+            rebuild_row2(tp);
+            tm = mul_nn_2(mul_dn_2(Uin.load(nu, op, lmn >> 1), Uin.load(mu, op, lmn >> 1)),
+                          Uin.load(nu, par, lmn_pm >> 1));
+            rebuild_row2(tm);
+        } else {
+            tp = mul_nd(mul_nn(Uin.load(nu, par, h), Uin.load(mu, op, lpn >> 1)), Uin.load(nu, op, lpm >> 1));
+            tm = mul_nn(mul_dn(Uin.load(nu, op, lmn >> 1), Uin.load(mu, op, lmn >> 1)), Uin.load(nu, par, lmn_pm >> 1));
+        }
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -634,15 +654,13 @@ mgq_status mgq_prolongate_batched(const mgq_lattice* coarse, mgq_lattice* fine, 
                     (unsigned long long)need);
     cudaStream_t st = as_stream(stream);
     const PbState S = pb_state_at(work, fine, n);
-    void** scratch = new void*[n];
+    std::vector<void*> scratch(n);
     char* p = static_cast<char*>(work) + pb_state_bytes(fine, n);
     for (int i = 0; i < n; i++) {
         scratch[i] = p;
         p += round256(links_bytes(&fine[i]));
     }
-    s = prolong_run(coarse, fine, scratch, n, c, rel_tol, max_iter, iter_budget, S, st);
-    delete[] scratch;
-    if (s) return s;
+    if ((s = prolong_run(coarse, fine, scratch.data(), n, c, rel_tol, max_iter, iter_budget, S, st))) return s;
     if (iters_out && (s = deliver_int(S.iters, iters_out, 3 * (size_t)n, st, "mgq_prolongate_batched"))) return s;
     if (sd_out && (s = deliver(S.sd, sd_out, 3 * (size_t)n, st, "mgq_prolongate_batched"))) return s;
     if (n_done_out && (s = deliver_int(S.ndone, n_done_out, 1, st, "mgq_prolongate_batched"))) return s;
