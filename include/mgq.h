@@ -19,7 +19,7 @@
  *   Argument errors are detected before any work is queued.
  * Lattice (Sec. III): D = 4 hypercube with extents dims[0..3] (all even,
  *   >= 2), periodic boundary conditions, V = dims[0]*dims[1]*dims[2]*dims[3]
- *   sites.  Site (x0,x1,x2,x3) has lexicographic index
+ *   <= 2^28 sites (128^4; 51.5 GB of links in the 12-real FP32 format).  Site (x0,x1,x2,x3) has lexicographic index
  *   x0 + L0*(x1 + L1*(x2 + L2*x3)) and parity (x0+x1+x2+x3) mod 2.
  *
  * Device link layout (owned by the caller, written by the library)
@@ -77,7 +77,7 @@ typedef enum { MGQ_PERIODIC = 0, MGQ_OPEN = 1 } mgq_bc;   /* periodic only (Sec.
 
 /* One lattice and the caller's device buffers for it. */
 typedef struct mgq_lattice {
-    int32_t dims[4];       /* L0..L3, each even and >= 2                           */
+    int32_t dims[4];       /* L0..L3, each even and >= 2; product <= 2^28          */
     int32_t bc[4];         /* mgq_bc per direction; only MGQ_PERIODIC is supported */
     int32_t prec;          /* mgq_prec: storage and arithmetic format of the links */
     int32_t action;        /* mgq_action                                           */

@@ -56,6 +56,7 @@ _SIGS = {
     "orc_heatbath_sweep": (None, [_D, _I, _dbl, _u64, _u32, _u64, _int, _U8]),
     "orc_heatbath_subsweep": (None, [_D, _I, _dbl, _u64, _u32, _u64, _int, _int, _int, _U8]),
     "orc_heatbath_one_link": (None, [_D, _I, _dbl, _u64, _u32, _u64, _int, _long, _int, _D, _U8]),
+    "orc_heatbath_link_staple": (None, [_D, _D, _dbl, _u64, _u32, _u64, _int, _long, _int, _D, _U8]),
     "orc_overrelax_sweep": (None, [_D, _I]),
     "orc_overrelax_one_link": (None, [_D, _I, _long, _int, _D]),
     "orc_overrelax_subsweep": (None, [_D, _I, _int, _int]),
@@ -225,6 +226,19 @@ def heatbath_one_link(U, dims, beta, seed, lattice_id, sweep, n_hb, s, mu):
     dec = np.zeros(3, dtype=np.uint8)
     lib().orc_heatbath_one_link(_dp(U.view(np.float64)), _dims(dims), float(beta), seed, lattice_id, sweep,
                                 int(n_hb), int(s), int(mu), _dp(out.view(np.float64)), dec.ctypes.data_as(_U8))
+    return out, dec
+
+
+def heatbath_link_staple(Ul, A, beta, seed, lattice_id, sweep, n_hb, s, mu):
+    """Heat-bath result for link Ul (3x3) with staple A (3x3) at lexicographic
+    site s, direction mu: heatbath_one_link without the lattice."""
+    out = np.zeros((3, 3), dtype=np.complex128)
+    dec = np.zeros(3, dtype=np.uint8)
+    Ul = np.ascontiguousarray(Ul, dtype=np.complex128)
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    lib().orc_heatbath_link_staple(_dp(Ul.view(np.float64)), _dp(A.view(np.float64)), float(beta), seed,
+                                   lattice_id, sweep, int(n_hb), int(s), int(mu), _dp(out.view(np.float64)),
+                                   dec.ctypes.data_as(_U8))
     return out, dec
 
 

@@ -599,6 +599,20 @@ void orc_heatbath_one_link(const double* U, const int* dims, double beta, uint64
     memcpy(Uout, &Un, sizeof Un);
 }
 
+/* The heat-bath result for a link U_in with staple A_in (both 3x3, row-major
+ * complex), as the link of direction mu at lexicographic site s_lex would get
+ * it in the given sweep: the same map as orc_heatbath_one_link with the staple
+ * supplied by the caller, for links of lattices too large to hold here. */
+void orc_heatbath_link_staple(const double* Uin, const double* Ain, double beta, uint64_t seed, uint32_t lattice_id,
+                              uint64_t sweep, int n_hb, long s_lex, int mu, double* Uout, uint8_t* dec)
+{
+    mat3 Ul, A;
+    memcpy(&Ul, Uin, sizeof Ul);
+    memcpy(&A, Ain, sizeof A);
+    mat3 Un = hb_link(Ul, A, beta, n_hb, seed, lattice_id, s_lex, mu, sweep, dec);
+    memcpy(Uout, &Un, sizeof Un);
+}
+
 /* One overrelaxation sweep on the same checkerboard schedule (no RNG). */
 void orc_overrelax_sweep(double* U, const int* dims)
 {

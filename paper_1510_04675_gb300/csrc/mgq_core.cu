@@ -34,7 +34,9 @@ bool valid_dims(const int32_t dims[4]) {
         if (dims[mu] < 2 || (dims[mu] & 1)) return false;
         V *= (uint64_t)dims[mu];
     }
-    return V <= (uint64_t(1) << 30);
+    // every index a kernel forms in 32 bits (links 4V, algebra entries 8 V/2,
+    // plaquettes 6V / 2) stays below 2^31
+    return V <= (uint64_t(1) << 28);
 }
 
 uint64_t site_stride(const int32_t dims[4]) {
@@ -78,7 +80,7 @@ uint64_t workspace_bytes(const mgq_lattice* lat) {
 mgq_status check_lattice(const mgq_lattice* lat, bool need_work, const char* fn) {
     if (!lat) return fail(MGQ_EINVAL, "%s: lattice is NULL", fn);
     if (!valid_dims(lat->dims))
-        return fail(MGQ_EINVAL, "%s: extents %d x %d x %d x %d must be even, >= 2, volume <= 2^30", fn, lat->dims[0],
+        return fail(MGQ_EINVAL, "%s: extents %d x %d x %d x %d must be even, >= 2, volume <= 2^28", fn, lat->dims[0],
                     lat->dims[1], lat->dims[2], lat->dims[3]);
     for (int mu = 0; mu < 4; mu++) {
         if (lat->bc[mu] == MGQ_OPEN) return fail(MGQ_EUNSUPPORTED, "%s: only periodic boundary conditions are built", fn);

@@ -267,7 +267,7 @@ struct Geom {
 // Division by an invariant integer through a multiply-high (Granlund and
 // Montgomery, PLDI 1994): for 2^(l-1) < L <= 2^l and m = ceil(2^(31+l) / L),
 // floor(n / L) = floor(n m / 2^(31+l)) for every 0 <= n < 2^31; the product's
-// high word shifted right by l - 1 gives it.  Site indices stay below 2^30.
+// high word shifted right by l - 1 gives it.  Site indices stay below 2^28.
 inline void set_divisors(Geom& g) {
     for (int d = 0; d < 3; d++) {
         const unsigned long long L = (unsigned long long)g.L[d];

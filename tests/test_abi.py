@@ -55,6 +55,10 @@ def test_sizes(mgqlib):
     assert mgqlib.mgq_links_bytes(ctypes.byref(c)) == 4 * 2 * 9 * S * 16
     assert mgqlib.mgq_links_bytes(ctypes.byref(_lat((3, 4, 4, 4)))) == 0
     assert mgqlib.mgq_links_bytes(ctypes.byref(_lat((4, 4, 4, 4), 7))) == 0
+    # the largest accepted volume is 2^28 sites (128^4); one more factor of two is refused
+    assert mgqlib.mgq_links_bytes(ctypes.byref(_lat((128, 128, 128, 128), 2))) == 4 * 2 * 6 * 2**27 * 8
+    assert mgqlib.mgq_links_bytes(ctypes.byref(_lat((256, 128, 128, 128), 2))) == 0
+    assert mgqlib.mgq_site_stride((ctypes.c_int32 * 4)(128, 128, 128, 256)) == 0
 
 
 @pytest.mark.parametrize("dims,prec,bc,status", [
@@ -63,6 +67,7 @@ def test_sizes(mgqlib):
     ((4, 4, 4, 4), 5, (0, 0, 0, 0), 1),   # bad precision
     ((4, 4, 4, 4), 0, (1, 0, 0, 0), 4),   # open boundary: unsupported
     ((4, 4, 4, 4), 0, (0, 0, 2, 0), 1),
+    ((128, 256, 128, 128), 2, (0, 0, 0, 0), 1),  # volume 2^29 > 2^28
 ])
 def test_host_side_rejections(mgqlib, dims, prec, bc, status):
     c = _lat(dims, prec, bc)

@@ -133,3 +133,20 @@ def test_heatbath_one_link_matches_subsweep(orc):
             continue
         Un, d = orc.heatbath_one_link(U, dims, 6.0, 10, 1, 4, 1, s, 2)
         assert np.array_equal(Un, B[s, 2]) and np.array_equal(d, dec[s, 2])
+
+
+def test_heatbath_link_staple_matches_one_link(orc):
+    """The lattice-free form (link and staple supplied) is the same map, bit for
+    bit; on a cold start every staple is 6 x identity."""
+    dims = [4, 2, 4, 2]
+    U = orc.init_links(dims, 1, seed=12)
+    for s in range(0, U.shape[0], 3):
+        for mu in (0, 3):
+            ref, dref = orc.heatbath_one_link(U, dims, 6.0, 12, 2, 7, 2, s, mu)
+            got, d = orc.heatbath_link_staple(U[s, mu], orc.staple(U, dims, s, mu), 6.0, 12, 2, 7, 2, s, mu)
+            assert np.array_equal(got, ref) and np.array_equal(d, dref)
+    C = orc.init_links(dims, 0)
+    assert np.array_equal(orc.staple(C, dims, 5, 1), 6 * np.eye(3))
+    ref, _ = orc.heatbath_one_link(C, dims, 6.0, 12, 0, 1, 1, 5, 1)
+    got, _ = orc.heatbath_link_staple(np.eye(3), 6 * np.eye(3), 6.0, 12, 0, 1, 1, 5, 1)
+    assert np.array_equal(got, ref)
