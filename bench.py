@@ -64,8 +64,12 @@ def parse_args():
     p.add_argument("--no-extras", action="store_true", help="skip the FP64/FP32 comparison legs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-large", action="store_true", help="skip the bounded 48^4 FP32/FP64 leg")
-    p.add_argument("--profile-window", choices=["steps", "force"], default="steps",
-                   help="what cudaProfilerStart/Stop bracket: the timed steps or the force timing")
+    p.add_argument("--profile-window", choices=["steps", "force", "batched", "prolongation"], default="steps",
+                   help="what cudaProfilerStart/Stop bracket: the timed steps, the force timing, one "
+                        "compound sweep of the batched leg, or the batched leg's host-polled prolongation")
+    p.add_argument("--legs", default="all",
+                   help="comma-separated extra legs to run (batched, multilevel_8_16_32, hmc_24, "
+                        "multiscale_16, flow_24x48, large_48), or all")
     return p.parse_args()
 
 
@@ -180,6 +184,9 @@ KERNEL_SOURCES = {
     "k_overrelax": "mgq_core.cu",
     "k_heatbath": "mgq_core.cu",
     "k_force": "mgq_hmc.cu",
+    "k_overrelax_batched": "mgq_batch.cu",
+    "k_ape_pb": "mgq_prolong.cu",
+    "k_sd_pb": "mgq_prolong.cu",
 }
 _COMMON = ["mgq_device.cuh", "mgq_stencil.cuh", "mgq_internal.h"]
 
@@ -349,7 +356,10 @@ def _graph_of(fn):
     return g
 
 
-def batched_leg(api, peak_gbs, beta_lo=5.8, beta_hi=6.1, n_sweeps=20, n_or=4, seed=4242):
+BATCHED_TAG = "batched_256_f32c12"
+
+
+def batched_leg(api, peak_gbs, beta_lo=5.8, beta_hi=6.1, n_sweeps=20, n_or=4, seed=4242, profile=None):
     """256 fine lattices (96 x 12^4, 96 x 16^4, 64 x 8^3x16, FP32 12-real) prolongated
     from coarse lattices thermalised at beta in [5.8, 6.1] with the paper's 0.001 %
     stopping rule on the device (mgq_prolongate_batched), then n_sweeps compound
@@ -372,7 +382,11 @@ def batched_leg(api, peak_gbs, beta_lo=5.8, beta_hi=6.1, n_sweeps=20, n_or=4, se
     cache = os.path.join(tempfile.mkdtemp(prefix="mgq_tune_"), "tune.json")
     shapes_ape = tune.autotune_ape(pb, cache_path=cache)
     # the stopping rule on the device, the host reading the finished count every 32 iterations
+    if profile == "prolongation":
+        torch.cuda.profiler.start()
     _, t_pro = _timed(lambda: api.mgq_prolongate_batched(pb, 0.05, 1e-5, 10000))
+    if profile == "prolongation":
+        torch.cuda.profiler.stop()
     iters = pb.iters.cpu().numpy()
     budget = int(iters.sum(axis=1).max()) + 3
     batch = api.Batch(fine, betas, max_sweeps=n_sweeps)
@@ -402,6 +416,11 @@ def batched_leg(api, peak_gbs, beta_lo=5.8, beta_hi=6.1, n_sweeps=20, n_or=4, se
         ms_all.append(a.elapsed_time(b))
         ms_sw.append(b.elapsed_time(c))
     ms_all, ms_sw = sorted(ms_all)[1], sorted(ms_sw)[1]
+    if profile == "batched":  # one compound sweep outside the graph: the window of ncu --profile-from-start off
+        torch.cuda.profiler.start()
+        api.mgq_update_sweeps_batched(batch, 100, 1, 1, n_or)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     V = sum(int(np.prod(x)) for x in shapes)
     sec = ms_sw * 1e-3
     bytes_per_sweep = 8 * (1 + n_or) * 9 * 48 * (V // 2)   # 9 link transfers per update, 12-real links
@@ -412,6 +431,12 @@ def batched_leg(api, peak_gbs, beta_lo=5.8, beta_hi=6.1, n_sweeps=20, n_or=4, se
                          "frac": achieved / peak_gbs, "traffic": None,
                          "algorithmic_bytes_per_sweep": bytes_per_sweep,
                          "note": "all 40 sub-sweep launches of a compound sweep over the 256 lattices"},
+            # DRAM bytes of one batched overrelaxation sub-sweep launch from an ncu capture of
+            # the current sources, beside its algorithmic bytes; a launch covers at most 128
+            # lattices, the captured one the first 128 (96 x 12^4 + 32 x 16^4)
+            "or_launch": {"lattices": min(128, len(shapes)),
+                          "algorithmic_bytes": 9 * 48 * (sum(int(np.prod(x)) for x in shapes[:128]) // 2),
+                          "traffic": traffic_from_profiles("k_overrelax_batched", BATCHED_TAG)},
             "prolongation": {"ms_host_polled": 1e3 * t_pro, "ms_in_graph": ms_all - ms_sw,
                              "iteration_budget": budget, "ape_steps_max": [int(v) for v in iters.max(axis=0)],
                              "ape_steps_mean": [float(v) for v in iters.mean(axis=0)],
@@ -867,10 +892,14 @@ def run_mgq(args, dims, world, rank, local):
         out["speedup_vs_fp64"] = (value / world) / out["fp64_plain_link_updates_per_s"]
         del lat, host_links
         torch.cuda.empty_cache()
-        legs = [("batched", lambda a: batched_leg(a, peak)), ("multilevel_8_16_32", multilevel_leg),
-                ("hmc_24", hmc_leg), ("multiscale_16", multiscale_leg), ("flow_24x48", flow_leg)]
+        legs = [("batched", lambda a: batched_leg(a, peak, profile=args.profile_window)),
+                ("multilevel_8_16_32", multilevel_leg), ("hmc_24", hmc_leg), ("multiscale_16", multiscale_leg),
+                ("flow_24x48", flow_leg)]
         if not args.no_large:
             legs.append(("large_48", lambda a: large_leg(a, peak)))
+        if args.legs != "all":
+            keep = set(args.legs.split(","))
+            legs = [(n, f) for n, f in legs if n in keep]
         for name, fn in legs:
             try:
                 out[name] = fn(api)
