@@ -762,7 +762,8 @@ def run_mgq(args, dims, world, rank, local):
         "gpu_launches": K * (8 + 8 * n_or + 1),
         "ms_overrelax_sweep_with_plaquette": last_ms,
         "clocks": clocks,
-        "launch_shapes": {"threads_per_block": launch_shapes,
+        "launch_shapes": {"threads_per_block": {"heatbath": tune.STAGED_THREADS, "overrelax": tune.STAGED_THREADS}
+                          if args.prec == "f32c12" and V // 2 >= tune.STAGED_MIN_VH else launch_shapes,
                           "tuned_by": "fixed: staged FP32 12-real sub-sweeps (V/2 >= 49152)"
                           if args.prec == "f32c12" and V // 2 >= tune.STAGED_MIN_VH else "paper_1510_04675_gb300.tune"},
     }
