@@ -208,7 +208,8 @@ uint64_t mgq_batch_workspace_bytes(const mgq_lattice* lats, int n_lat, int n_swe
  * every lattice's FP64 average plaquette after each compound sweep (measured
  * by the last overrelaxation sweep, as in mgq_update_sweeps) and then
  * needs batch_work (device, 256-B aligned, >= mgq_batch_workspace_bytes).
- * Errors: MGQ_EINVAL (mixed precision, bad beta, ...), MGQ_ENOMEM. */
+ * Errors: MGQ_EINVAL (no lattice: n_lat < 1; mixed precision, bad beta, ...),
+ * MGQ_ENOMEM. */
 mgq_status mgq_update_sweeps_batched(mgq_lattice* lats, int n_lat, const double* betas, uint64_t sweep0,
                                      int n_sweeps, int n_hb, int n_or, double* plaq_out, void* batch_work,
                                      uint64_t batch_work_bytes, void* stream);
@@ -432,7 +433,7 @@ uint64_t mgq_prolongate_batched_workspace_bytes(const mgq_lattice* fine, int n);
  * sd_out (3n doubles) and n_done_out (the number of finished lattices, 1 int):
  * host or device, NULL to skip (a host pointer synchronises the stream).
  * work: device, 256-byte aligned, >= mgq_prolongate_batched_workspace_bytes.
- * Errors: MGQ_EINVAL, MGQ_ENOMEM. */
+ * Errors: MGQ_EINVAL (no pair: n < 1; extents, precisions, ...), MGQ_ENOMEM. */
 mgq_status mgq_prolongate_batched(const mgq_lattice* coarse, mgq_lattice* fine, int n, double c, double rel_tol,
                                   int max_iter, int iter_budget, int* iters_out, double* sd_out, int* n_done_out,
                                   void* work, uint64_t work_bytes, void* stream);

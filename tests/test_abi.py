@@ -117,3 +117,21 @@ def test_adaptive_flow_host_helpers(mgqlib):
     assert f(-1.0, 0.25) == -1 and f(1.0, 0.0) == -1 and f(float("nan"), 0.25) == -1
     c = _lat((8, 8, 8, 8), 2)
     assert _lib.load().mgq_flow_adaptive_scratch_bytes(ctypes.byref(c)) == 4 * 2 * 8 * 8**4 // 2 * 4
+
+
+def test_empty_batches_are_refused(mgqlib):
+    """A batch of no lattices is an argument error, refused before any work is queued."""
+    c = _lat()
+    c.links = 1 << 20
+    betas = (ctypes.c_double * 1)(6.0)
+    assert mgqlib.mgq_batch_workspace_bytes(ctypes.byref(c), 0, 1) == 0
+    assert mgqlib.mgq_update_sweeps_batched(ctypes.byref(c), 0, betas, ctypes.c_uint64(0), 1, 1, 4, None, None,
+                                            ctypes.c_uint64(0), None) == 1
+    assert b"at least one" in mgqlib.mgq_last_error()
+    f = _lat((8, 8, 8, 8))
+    f.links = 1 << 20
+    assert mgqlib.mgq_prolongate_batched_workspace_bytes(ctypes.byref(f), 0) == 0
+    assert mgqlib.mgq_prolongate_batched(ctypes.byref(c), ctypes.byref(f), 0, ctypes.c_double(0.05),
+                                         ctypes.c_double(1e-5), 100, 0, None, None, None, None,
+                                         ctypes.c_uint64(0), None) == 1
+    assert b"at least one" in mgqlib.mgq_last_error()

@@ -253,3 +253,32 @@ def test_overrelax_sweep_with_plaquette(gpu, orc, prec, tol, dims):
             assert abs(p - orc.plaquette(U, dims)) < 1e-12
     plaq = gpu.mgq_update_sweeps(b, 5.8, 9, 2, 1, 3, plaq_out=True)
     assert abs(plaq[-1] - gpu.mgq_plaquette(b)) < tol
+
+
+def test_zero_sweeps_change_nothing(gpu):
+    """Degenerate counts: no compound sweep leaves every link as it was, single
+    and batched, with an empty plaquette record."""
+    lats = [_lat(gpu, d, "f32c12", seed=11 + i, lid=i) for i, d in enumerate([[4, 4, 4, 4], [6, 4, 2, 8]])]
+    for l in lats:
+        gpu.mgq_init_links(l, 1)
+    before = [l.links.clone() for l in lats]
+    rec = gpu.mgq_update_sweeps(lats[0], 6.0, 0, 0, 1, 4, plaq_out=True)
+    assert rec.size == 0
+    B = gpu.Batch(lats, [6.0, 5.9])
+    gpu.mgq_update_sweeps_batched(B, 0, 0, 1, 4)
+    torch.cuda.synchronize()
+    for l, b in zip(lats, before):
+        assert torch.equal(l.links, b)
+
+
+def test_heatbath_only_sweeps_parity(gpu, orc):
+    """n_or = 0: compound sweeps of the heat bath alone, the plaquette then taken
+    by the plaquette kernel (FP64: links 1e-12, plaquettes 1e-13)."""
+    dims, beta = [4, 6, 4, 2], 5.8
+    U = orc.init_links(dims, 1, seed=19)
+    lat = _lat(gpu, dims, seed=19)
+    lat.from_numpy(U)
+    ref = orc.update_chain(U, dims, beta, 19, 0, 4, 2, 1, 0)
+    got = gpu.mgq_update_sweeps(lat, beta, 4, 2, 1, 0, plaq_out=True)
+    assert np.max(np.abs(got - ref)) < 1e-13
+    assert np.max(np.abs(lat.to_numpy() - U)) < 1e-12
