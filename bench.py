@@ -185,8 +185,7 @@ KERNEL_SOURCES = {
     "k_heatbath": "mgq_core.cu",
     "k_force": "mgq_hmc.cu",
     "k_overrelax_batched": "mgq_batch.cu",
-    "k_ape_pb": "mgq_prolong.cu",
-    "k_sd_pb": "mgq_prolong.cu",
+    "k_iter_pb": "mgq_prolong.cu",
 }
 _COMMON = ["mgq_device.cuh", "mgq_stencil.cuh", "mgq_internal.h"]
 

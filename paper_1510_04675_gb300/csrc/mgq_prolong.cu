@@ -83,19 +83,17 @@ __global__ void k_restrict(Links<T, NP> Uf, Geom gf, Links<T, NP> Uc, Geom gc) {
 // ======================================================= interpolation stages
 // The stages run as a device-side state machine per lattice, so that neither
 // the stopping rule nor the stage changes need the host: every iteration is
-// two launches over all lattices of a call --
-//   k_ape_pb      one Jacobi APE step of the lattice's current stage (buffer
-//                 cur -> 1 - cur), or, at the start of a stage, the copy of the
-//                 previous stage's bonds into the other buffer;
-//   k_sd_pb       the partial action S_d of the lattice's newest field; the
-//                 last block of a lattice to finish (atomic ticket, no waiting)
-//                 sums the per-block partials in a fixed order and advances the
-//                 lattice's state: stop after the first step with
-//                 |S_d(k) - S_d(k-1)| <= rel_tol |S_d(k-1)| or after max_iter
-//                 steps (rel_tol <= 0: exactly max_iter), then the next stage.
-// A stage of k steps takes k + 1 iterations (one to measure its start field);
-// a finished lattice turns every later launch into a no-op.  Launches carry
-// the lattice table as a kernel parameter; the state lives in the workspace.
+// one launch of k_iter_pb over all lattices of a call (up to PB_CHUNK per
+// launch), in which one set of blocks measures the partial action S_d of a
+// lattice's newest field while another takes the next Jacobi APE step from
+// it; the last block of a lattice to finish (atomic ticket, no waiting) sums
+// the partials in a fixed order and advances the lattice's state: stop after
+// the first step k with |S_d(k) - S_d(k-1)| <= rel_tol |S_d(k-1)| or after
+// max_iter steps (rel_tol <= 0: exactly max_iter), then the next stage.
+// A stage of k steps takes k + 1 iterations (the first measures its start
+// field); a finished lattice turns every later launch into a no-op.  Launches
+// carry the lattice table as a kernel parameter; the state lives in the
+// workspace.
 
 struct ProlongCtl {
     int d;        // current stage 0..2; 3 when finished
@@ -111,7 +109,7 @@ static_assert(sizeof(ProlongCtl) == 64, "control block layout");
 
 constexpr int PB_CHUNK = 64;       // lattices per launch (kernel-parameter table)
 constexpr int PB_THREADS = 128;
-constexpr int PB_SD_THREADS = 256;
+constexpr int PB_SD_LANES = 256;  // partial-action lanes per block (any block size)
 constexpr int PB_SD_MAXBLK = 512;  // partial-action blocks per lattice
 
 template <class T>
@@ -125,8 +123,8 @@ template <class T>
 struct PBatch {
     int n;
     int prefix[PB_CHUNK + 1];   // blocks of the all-bond kernels (8 Vh_f bonds each)
-    int aprefix[PB_CHUNK + 1];  // blocks of the APE kernel (the largest stage set, 24 V_c bonds)
-    int sprefix[PB_CHUNK + 1];  // blocks of the partial-action kernel
+    int aprefix[PB_CHUNK + 1];  // bond blocks of the iteration kernel (the largest stage set, 24 V_c bonds)
+    int sprefix[PB_CHUNK + 1];  // partial-action blocks of the iteration kernel (first in its grid)
     ProDesc<T> d[PB_CHUNK];
     ProlongCtl* ctl;            // [n]
     double* partials;           // [sprefix[n]]
@@ -256,34 +254,17 @@ __device__ __forceinline__ void plaq_of(const Geom& gc, int d, int t, int& mu, i
     fine_site(yc, mu, p & 1, nu, (p >> 1) & 1, mask, x);
 }
 
-// One iteration's bond work.  Stepping (phase 1): every bond with
-// chi_mu(n) = d + 1 gets Unew = P_SU(3)[U + c sum_{nu != mu, n_nu odd}
-// (T+_munu + T-_munu)] (Eq. APE), T+ = U_nu(n) U_mu(n+nu) U_nu(n+mu)^+,
-// T- = U_nu(n-nu)^+ U_mu(n-nu) U_nu(n-nu+mu), read from buffer cur and written
-// to 1 - cur (Jacobi); no other bond changes within a stage.  Stage start
-// (phase 0, d >= 1): the bonds of the previous stage (chi_mu = d) are copied
-// from cur to 1 - cur, so that both buffers agree outside the new stage's bonds.
+// One Jacobi APE step on bond t of the set chi_mu(n) = k: Unew = P_SU(3)[U + c
+// sum_{nu != mu, n_nu odd} (T+_munu + T-_munu)] (Eq. APE), T+ = U_nu(n) U_mu(n+nu)
+// U_nu(n+mu)^+, T- = U_nu(n-nu)^+ U_mu(n-nu) U_nu(n-nu+mu), read from Uin and
+// written to Uout; no other bond changes within a stage.
 template <class T, int NP>
-__global__ void __launch_bounds__(PB_THREADS, sizeof(T) == 8 ? 1 : 5) k_ape_pb(const __grid_constant__ PBatch<T> B) {
-    pdl_launch_dependents();
-    pdl_wait();  // the state and the fields come from the previous launch
-    const int l = find_block(B.aprefix, B.n, blockIdx.x);
-    const ProDesc<T>& D = B.d[l];
-    const ProlongCtl* C = B.ctl + l;
-    const int d = C->d, phase = C->phase, cur = C->cur;
-    if (d >= 3 || (phase == 0 && d == 0)) return;
-    const int k = phase == 0 ? d : d + 1;  // chi_mu of the bonds this iteration touches
-    const int t = (blockIdx.x - B.aprefix[l]) * (int)blockDim.x + threadIdx.x;
-    if (t >= n_bonds(D.gc, k)) return;
+__device__ __forceinline__ void ape_bond(const ProDesc<T>& D, T c, int k, int t, const Links<T, NP>& Uin,
+                                         const Links<T, NP>& Uout) {
     const Geom& g = D.gf;
     int mu, x[4];
     bond_of(D.gc, k, t, mu, x);
     const int par = (x[0] + x[1] + x[2] + x[3]) & 1, h = lex_of(g, x) >> 1;
-    const Links<T, NP> Uin = field<T, NP>(D.buf[cur], g), Uout = field<T, NP>(D.buf[cur ^ 1], g);
-    if (phase == 0) {
-        Uout.store(mu, par, h, Uin.load(mu, par, h));
-        return;
-    }
     const int op = par ^ 1;
     M3<T> M = Uin.load(mu, par, h);
     const int lpm = lex_hop(g, x, mu, +1);
@@ -309,10 +290,20 @@ __global__ void __launch_bounds__(PB_THREADS, sizeof(T) == 8 ? 1 : 5) k_ape_pb(c
 #pragma unroll
             for (int j = 0; j < 3; j++) {
                 const Cx<T> sum = tp.e[i][j] + tm.e[i][j];
-                M.e[i][j] = M.e[i][j] + scale(sum, B.c);
+                M.e[i][j] = M.e[i][j] + scale(sum, c);
             }
     }
     Uout.store(mu, par, h, su3_project(M));
+}
+
+// bond t of the set chi_mu(n) = k copied from Uin to Uout
+template <class T, int NP>
+__device__ __forceinline__ void copy_bond(const ProDesc<T>& D, int k, int t, const Links<T, NP>& Uin,
+                                          const Links<T, NP>& Uout) {
+    int mu, x[4];
+    bond_of(D.gc, k, t, mu, x);
+    const int par = (x[0] + x[1] + x[2] + x[3]) & 1, h = lex_of(D.gf, x) >> 1;
+    Uout.store(mu, par, h, Uin.load(mu, par, h));
 }
 
 // Re Tr of the plaquette U_mu(x) U_nu(x+mu) (U_nu(x) U_mu(x+nu))^+.  FP32: from
@@ -340,59 +331,127 @@ __device__ __forceinline__ T plaq_retr(const Links<T, NP>& U, int mu, int nu, in
     }
 }
 
-// S_d / beta = sum over plaquettes with chi_munu(n) = d of (1 - Re Tr U_p / 3)
-// (Eq. smoothing) of the lattice's newest field, and the state update.
+// Sum of PB_SD_LANES = 256 values in lanes[] (shared) in the order a 256-thread
+// block_sum takes them (warp-shuffle trees over eight warps of 32 lanes, then
+// over the eight warp sums), computed by warp 0 of a block of any size; the
+// result is valid in thread 0.  The partial action thus does not depend on the
+// launch shape.
+__device__ __forceinline__ double lanes_sum(const double* lanes) {
+    __shared__ double warp_part[PB_SD_LANES / 32];
+    double v = 0.0;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+#pragma unroll
+        for (int w = 0; w < PB_SD_LANES / 32; w++) {
+            double x = lanes[32 * w + lane];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) warp_part[w] = x;
+        }
+        __syncwarp();
+        v = lane < PB_SD_LANES / 32 ? warp_part[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+// One iteration of every lattice of the launch.  The grid holds the
+// partial-action blocks of all its lattices, then their bond blocks (so that
+// the partial actions, chains of dependent loads, start first and overlap the
+// steps):
+//   partial-action blocks: S_d / beta = sum over the plaquettes with
+//     chi_munu(n) = d of (1 - Re Tr U_p / 3) (Eq. smoothing) of the newest
+//     field (buffer cur), 256 lanes per block whatever the block size (lane v
+//     of block b takes the plaquettes b 256 + v + j nS 256 in turn);
+//   bond blocks: the next APE step of stage d (bonds with chi_mu = d + 1) from
+//     cur into 1 - cur, and at the start of a stage d >= 1 (phase 0) also the
+//     copy of the previous stage's bonds (chi_mu = d) from cur to 1 - cur, so
+//     that both buffers agree outside the stage's bonds.
+// Both read only buffer cur.  The step is taken before the partial action of
+// its predecessor is known; when that partial action ends the stage, the step
+// is dropped (cur keeps the stage's last step, and the next stage's copy
+// overwrites the dropped bonds in 1 - cur).  The last block of a lattice to
+// finish (atomic ticket over all its blocks) sums the partials in a fixed order
+// and advances the state: after the start field's S_d (phase 0) the stage's
+// first step is the newest field; after a step's S_d the stage stops when
+// |S_d(k) - S_d(k-1)| <= rel_tol |S_d(k-1)| or k = max_iter (rel_tol <= 0:
+// exactly max_iter steps), else the step it has just taken becomes the newest.
 template <class T, int NP>
-__global__ void __launch_bounds__(PB_SD_THREADS) k_sd_pb(const __grid_constant__ PBatch<T> B) {
+__global__ void __launch_bounds__(PB_THREADS, sizeof(T) == 8 ? 1 : 5) k_iter_pb(const __grid_constant__ PBatch<T> B) {
     pdl_launch_dependents();
-    pdl_wait();
-    const int l = find_block(B.sprefix, B.n, blockIdx.x);
+    pdl_wait();  // the state and the fields come from the previous launch
+    const int nSall = B.sprefix[B.n];
+    const bool sd_role = (int)blockIdx.x < nSall;
+    const int l = sd_role ? find_block(B.sprefix, B.n, blockIdx.x) : find_block(B.aprefix, B.n, blockIdx.x - nSall);
     const ProDesc<T>& D = B.d[l];
     ProlongCtl* C = B.ctl + l;
     const int d = C->d, phase = C->phase, cur = C->cur;
-    if (d >= 3) return;
-    const Geom& g = D.gf;
-    const Links<T, NP> U = field<T, NP>(D.buf[phase == 1 ? cur ^ 1 : cur], g);
-    const int nb = B.sprefix[l + 1] - B.sprefix[l], b = blockIdx.x - B.sprefix[l];
-    const int np = n_plaqs(D.gc, d);
-    double acc = 0.0;
-    for (int t = b * PB_SD_THREADS + threadIdx.x; t < np; t += nb * PB_SD_THREADS) {
-        int mu, nu, x[4];
-        plaq_of(D.gc, d, t, mu, nu, x);
-        const int par = (x[0] + x[1] + x[2] + x[3]) & 1, h = lex_of(g, x) >> 1, op = par ^ 1;
-        const int hpm = lex_hop(g, x, mu, +1) >> 1, hpn = lex_hop(g, x, nu, +1) >> 1;
-        acc += 1.0 - (double)plaq_retr(U, mu, nu, par, op, h, hpm, hpn) / 3.0;
-    }
-    acc = block_sum(acc);
-    double* part = B.partials + B.sprefix[l];
+    if (d >= 3) return;  // the whole block: one lattice per block
+    __shared__ double lanes[PB_SD_LANES];
     __shared__ int last;
+    const Geom& g = D.gf;
+    const int nS = B.sprefix[l + 1] - B.sprefix[l], nA = B.aprefix[l + 1] - B.aprefix[l];
+    const int b = sd_role ? (int)blockIdx.x - B.sprefix[l] : (int)blockIdx.x - nSall - B.aprefix[l];
+    double* part = B.partials + B.sprefix[l];
+    const Links<T, NP> Uin = field<T, NP>(D.buf[cur], g);
+    if (sd_role) {
+        const int np = n_plaqs(D.gc, d);
+        for (int v = threadIdx.x; v < PB_SD_LANES; v += blockDim.x) {
+            double acc = 0.0;
+            for (int t = b * PB_SD_LANES + v; t < np; t += nS * PB_SD_LANES) {
+                int mu, nu, x[4];
+                plaq_of(D.gc, d, t, mu, nu, x);
+                const int par = (x[0] + x[1] + x[2] + x[3]) & 1, h = lex_of(g, x) >> 1, op = par ^ 1;
+                const int hpm = lex_hop(g, x, mu, +1) >> 1, hpn = lex_hop(g, x, nu, +1) >> 1;
+                acc += 1.0 - (double)plaq_retr(Uin, mu, nu, par, op, h, hpm, hpn) / 3.0;
+            }
+            lanes[v] = acc;
+        }
+        __syncthreads();
+        const double sb = lanes_sum(lanes);
+        if (threadIdx.x == 0) part[b] = sb;
+    } else {
+        const Links<T, NP> Uout = field<T, NP>(D.buf[cur ^ 1], g);
+        const int t0 = b * (int)blockDim.x + threadIdx.x, stride = nA * (int)blockDim.x;
+        if (phase == 0 && d >= 1)
+            for (int t = t0; t < n_bonds(D.gc, d); t += stride) copy_bond<T, NP>(D, d, t, Uin, Uout);
+        const int nstep = n_bonds(D.gc, d + 1);
+        for (int t = t0; t < nstep; t += stride) ape_bond<T, NP>(D, B.c, d + 1, t, Uin, Uout);
+    }
+    __syncthreads();  // every thread of the block has read the state and done its work
     if (threadIdx.x == 0) {
-        part[b] = acc;
         __threadfence();
-        last = atomicAdd(B.ticket + l, 1u) == (unsigned)(nb - 1);
+        last = atomicAdd(B.ticket + l, 1u) == (unsigned)(nS + nA - 1);
     }
     __syncthreads();
     if (!last) return;
     // the last block of this lattice: every partial is written; a fixed-order sum
     __threadfence();
-    double v = 0.0;
-    for (int i = threadIdx.x; i < nb; i += PB_SD_THREADS) v += __ldcg(part + i);
-    const double S = block_sum(v);
+    for (int v = threadIdx.x; v < PB_SD_LANES; v += blockDim.x) {
+        double sv = 0.0;
+        for (int i = v; i < nS; i += PB_SD_LANES) sv += __ldcg(part + i);
+        lanes[v] = sv;
+    }
+    __syncthreads();
+    const double S = lanes_sum(lanes);
     if (threadIdx.x != 0) return;
     B.ticket[l] = 0u;
     if (phase == 0) {
         C->prev = S;
-        C->it = 0;
-        if (B.max_iter > 0) {
+        if (B.max_iter > 0) {  // the first step, taken in this iteration, is the newest field
             C->phase = 1;
+            C->it = 1;
+            C->cur = cur ^ 1;
             return;
         }
+        C->it = 0;
     } else {
-        C->it += 1;
-        C->cur = cur ^ 1;
         const bool stop = (B.rel_tol > 0.0 && fabs(S - C->prev) <= B.rel_tol * fabs(C->prev)) || C->it >= B.max_iter;
         if (!stop) {
             C->prev = S;
+            C->it += 1;
+            C->cur = cur ^ 1;
             return;
         }
     }
@@ -426,11 +485,11 @@ __global__ void __launch_bounds__(PB_THREADS) k_finish_pb(const __grid_constant_
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
 // partial-action blocks of one lattice: one block per 1024 plaquettes (four per
-// thread) of the largest set (48 V_c = 3 V) for a lattice alone, up to
+// lane) of the largest set (48 V_c = 3 V) for a lattice alone, up to
 // PB_SD_MAXBLK; in a call over many lattices the lattice's share of about 4096
 // blocks, so that the blocks stay large when there is parallelism across lattices
 static int sd_blocks(const Geom& g, double total_sites) {
-    const long full = nblk(3L * g.V, 4 * PB_SD_THREADS);
+    const long full = nblk(3L * g.V, 4 * PB_SD_LANES);
     long b = (long)((4096.0 * g.V + total_sites - 1.0) / total_sites);
     if (b > full) b = full;
     if (b > PB_SD_MAXBLK) b = PB_SD_MAXBLK;
@@ -471,8 +530,10 @@ static void fill_pbatch(PBatch<T>& B, const mgq_lattice* coarse, const mgq_latti
         D.gf = make_geom(F.dims);
         D.gc = make_geom(coarse[first + i].dims);
         B.prefix[i + 1] = B.prefix[i] + nblk(8L * D.gf.Vh, PB_THREADS);
-        B.aprefix[i + 1] = B.aprefix[i] + nblk(24L * D.gc.V, block_size(MGQ_KERNEL_APE, F.prec));
-        B.sprefix[i + 1] = B.sprefix[i] + sd_blocks(D.gf, tsites);
+        // bond blocks for the largest stage set (24 V_c bonds); the copy at a stage start loops
+        const int nS = sd_blocks(D.gf, tsites), nA = nblk(24L * D.gc.V, block_size(MGQ_KERNEL_APE, F.prec));
+        B.aprefix[i + 1] = B.aprefix[i] + nA;
+        B.sprefix[i + 1] = B.sprefix[i] + nS;
     }
     B.ctl = S.ctl + first;
     B.partials = S.partials + poff;
@@ -511,8 +572,7 @@ static mgq_status prolong_run(const mgq_lattice* coarse, mgq_lattice* fine, void
     if ((s = cuda_check("prolongate: transfer"))) return s;
     auto iteration = [&]() {
         each_chunk([&]<class T, int NP>(const PBatch<T>& B, int) {
-            launch_pdl(k_ape_pb<T, NP>, B.aprefix[B.n], block_size(MGQ_KERNEL_APE, fine[0].prec), st, B);
-            launch_pdl(k_sd_pb<T, NP>, B.sprefix[B.n], PB_SD_THREADS, st, B);
+            launch_pdl(k_iter_pb<T, NP>, B.sprefix[B.n] + B.aprefix[B.n], block_size(MGQ_KERNEL_APE, fine[0].prec), st, B);
         });
     };
     if (budget > 0) {
