@@ -422,7 +422,7 @@ uint64_t mgq_prolongate_batched_workspace_bytes(const mgq_lattice* fine, int n);
 /* Prolongation (as mgq_prolongate) of n independent lattices of possibly
  * different extents at once -- the N_s configurations refined in parallel
  * (Sec. II) -- each with its own stage, step count and stopping decision on
- * the device.  Every APE iteration is two launches over all lattices; a stage
+ * the device.  Every APE iteration is one launch per 64 lattices; a stage
  * of k steps takes k + 1 iterations, so a lattice whose stages take k0, k1, k2
  * steps is finished after k0 + k1 + k2 + 3 iterations, and later iterations
  * leave it alone.  iter_budget = 0: iterate until every lattice finished (the
