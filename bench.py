@@ -565,12 +565,11 @@ def flow_leg(api, dims=(24, 24, 24, 48), beta=5.96, t0=2.79, prec="f32c12"):
             "t2E_at_t0": float(t0 * t0 * Ea[1])}
 
 
-def large_leg(api, peak_gbs, beta=6.2, n_sweeps=100, n_traj=10, n_flow=100):
+def large_leg(api, peak_gbs, beta=6.2, n_sweeps=100, n_traj=10, n_flow=300):
     """48^4 at beta = 6.2, FP32 12-real and FP64 side by side, bounded to stay within the
     default run: 100 x (1 HB + 1 OR) in FP32 (FP64: 2), 10 HMC trajectories of 40 steps
-    (FP64: 1), Wilson flow eps = 0.01 to t = 1 in FP32 (the workload asks for t = 3; FP64: 10
-    steps) with clover Q, and dQ/d omega of the flowed Q through checkpointed adjoint flow
-    steps.  The FP32-vs-FP64 errors come from the same configuration, the same Philox
+    (FP64: 1), Wilson flow eps = 0.01 to t = 3 in FP32 (FP64: 10 steps) with clover Q, and
+    dQ/d omega of the flowed Q through checkpointed adjoint flow steps.  The FP32-vs-FP64 errors come from the same configuration, the same Philox
     words and the same momenta in both formats."""
     import numpy as np
     import torch
