@@ -565,9 +565,9 @@ def flow_leg(api, dims=(24, 24, 24, 48), beta=5.96, t0=2.79, prec="f32c12"):
             "t2E_at_t0": float(t0 * t0 * Ea[1])}
 
 
-def large_leg(api, peak_gbs, beta=6.2, n_sweeps=100, n_traj=10, n_flow=300):
+def large_leg(api, peak_gbs, beta=6.2, n_sweeps=100, n_traj=10, n_flow=300, n_or=4):
     """48^4 at beta = 6.2, FP32 12-real and FP64 side by side, bounded to stay within the
-    default run: 100 x (1 HB + 1 OR) in FP32 (FP64: 2), 10 HMC trajectories of 40 steps
+    default run: 100 x (1 HB + 4 OR) in FP32 (FP64: 2), 10 HMC trajectories of 40 steps
     (FP64: 1), Wilson flow eps = 0.01 to t = 3 in FP32 (FP64: 10 steps) with clover Q, and
     dQ/d omega of the flowed Q through checkpointed adjoint flow steps.  The FP32-vs-FP64 errors come from the same configuration, the same Philox
     words and the same momenta in both formats."""
@@ -577,12 +577,12 @@ def large_leg(api, peak_gbs, beta=6.2, n_sweeps=100, n_traj=10, n_flow=300):
     from paper_1510_04675_gb300.autograd import flowed_observable
 
     V = 48**4
-    out = {"reductions": f"FP32: {n_sweeps} sweeps, {n_traj} trajectories, flow to t = {n_flow * 0.01:g}; "
+    out = {"reductions": f"FP32: {n_sweeps} x (1 HB + {n_or} OR), {n_traj} trajectories, flow to t = {n_flow * 0.01:g}; "
                          "FP64: 2 sweeps, 1 trajectory, 10 flow steps"}
     l32 = api.Lattice([48] * 4, "f32c12", seed=97, with_mom=True)
     api.mgq_init_links(l32, 1)
-    _, t_sw = _timed(lambda: api.mgq_update_sweeps(l32, beta, 0, n_sweeps, 1, 1))
-    r = 2 * 4 * V * n_sweeps / t_sw
+    _, t_sw = _timed(lambda: api.mgq_update_sweeps(l32, beta, 0, n_sweeps, 1, n_or))
+    r = (1 + n_or) * 4 * V * n_sweeps / t_sw
     out["f32c12"] = {"sweeps": n_sweeps, "link_updates_per_s": r, "hbm_gbs": r * 9 * 48 / 1e9,
                      "hbm_frac": r * 9 * 48 / 1e9 / peak_gbs}
     # the same configuration in FP64
@@ -592,12 +592,12 @@ def large_leg(api, peak_gbs, beta=6.2, n_sweeps=100, n_traj=10, n_flow=300):
     api.mgq_import_links(l64, canon)
     del canon
     start32, start64 = api.copy_lattice(l32), api.copy_lattice(l64)
-    _, t64 = _timed(lambda: api.mgq_update_sweeps(l64, beta, n_sweeps, 2, 1, 1))
-    out["f64"] = {"sweeps": 2, "link_updates_per_s": 2 * 4 * V * 2 / t64}
+    _, t64 = _timed(lambda: api.mgq_update_sweeps(l64, beta, n_sweeps, 2, 1, n_or))
+    out["f64"] = {"sweeps": 2, "link_updates_per_s": (1 + n_or) * 4 * V * 2 / t64}
     # one compound sweep from the same start with the same random words
-    p32 = api.mgq_update_sweeps(l32, beta, n_sweeps, 1, 1, 1, plaq_out=True)[0]
+    p32 = api.mgq_update_sweeps(l32, beta, n_sweeps, 1, 1, n_or, plaq_out=True)[0]
     s64 = api.copy_lattice(start64)
-    p64 = api.mgq_update_sweeps(s64, beta, n_sweeps, 1, 1, 1, plaq_out=True)[0]
+    p64 = api.mgq_update_sweeps(s64, beta, n_sweeps, 1, 1, n_or, plaq_out=True)[0]
     del s64
     # HMC: trajectories of 40 steps; trajectory 0 in both formats from the same start
     l32.links.copy_(start32.links)
