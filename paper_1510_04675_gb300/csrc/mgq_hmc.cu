@@ -46,12 +46,15 @@ __global__ void __launch_bounds__(STAGED_THREADS, 5) k_force_staged(Links<float,
     pdl_launch_dependents();
     const int mu = threadIdx.x >> 5, par = blockIdx.x & 1;
     const int h = (blockIdx.x >> 1) * 32 + (threadIdx.x & 31);
+    const int hc = h < g.Vh ? h : g.Vh - 1;  // lanes past the end compute a copy and store nothing
     int x[4];
-    cb_coords(g, par, h, x);
+    cb_coords(g, par, hc, x);
     pdl_wait();
-    if (h >= g.Vh) return;
     M3<float> u;
-    const M3<float> A = staple_staged(U, g, x, h, mu, par, sm, u);
+    // the four warps are the four directions at the same sites: U_nu(x) of the
+    // upper staple terms is the updated link of warp nu
+    const M3<float> A = staple_staged<NoWork, true>(U, g, x, hc, mu, par, sm, u);
+    if (h >= g.Vh) return;
     const M3<float> M = mul_nn(u, A);
     float t[8];
     ta_coeffs(M, t);

@@ -26,9 +26,9 @@ def test_force_parity_fp64(gpu, orc, dims):
     assert np.max(np.abs(got - ref)) < 1e-12
 
 
-@pytest.mark.parametrize("prec", ["f32", "f32c12"])
-def test_force_fp32(gpu, orc, prec):
-    dims = [24, 24, 24, 24] if prec == "f32c12" else [8, 8, 8, 8]
+@pytest.mark.parametrize("prec,dims", [("f32", [8, 8, 8, 8]), ("f32c12", [24, 24, 24, 24]),
+                                       ("f32c12", [6, 6, 6, 6])])   # 6^4: V/2 = 648, a partly filled 32-site band
+def test_force_fp32(gpu, orc, prec, dims):
     U = orc.init_links(dims, 1, seed=4)
     lat = gpu.Lattice(dims, prec)
     lat.from_numpy(U)
