@@ -37,27 +37,138 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_force(Links<T, 
     }
 }
 
-// FP32 12-real force with the staple's links staged through shared memory
-// (staple_staged): a block of 4 warps covers the 4 directions of one parity for
-// a 32-site band (block b: band b/2, parity b%2).
+// FP32 12-real force with the staple's links staged through shared memory (the
+// cp.async pipeline of staple_staged): a block of 4 warps covers the 4
+// directions of one parity for a 32-site band (block b: band b/2, parity b%2),
+// so warp mu, lane l holds U_mu(x) of the band's site l.
+//
+// Each of the six plaquettes at x is formed once.  The upper term of U_mu(x) in
+// plane nu, U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ = P_mu,nu(x), is the
+// adjoint of the upper term of U_nu(x) in plane mu, and TA(M^+) = -TA(M) with TA
+// linear, so
+//   TA(U_mu A_mu) = TA(U_mu A_mu^dn) + sum_{nu owned} TA(P_mu,nu) - sum_{nu other} TA(P_nu,mu)
+// where A^dn holds the three lower terms.  The owner of plane {mu, nu} is warp mu
+// when nu = mu + 1 (mod 4), or nu = mu + 2 with mu < 2: warp 0 forms P_01 and
+// P_02, warp 1 P_12 and P_13, warp 2 P_23, warp 3 P_30.  Owners leave their TA
+// coefficients in shared memory; the partner warp subtracts them after a
+// barrier.  Per site this is 12 lower and 6 upper staple terms where the plain
+// staple takes 12 of each.  The half-terms run lower first, then the owned
+// upper ones; U_nu(x) of an upper term is the updated link warp nu staged.
+//
+// Shared memory per thread column (STAGED_SMEM in all): two stages of three
+// staged links, the updated link in slot (2, 0); its row 2 is published in slot
+// (0, 2), which the upper terms leave free, and the TA coefficients of owned
+// plane j in slot (1, j) once stage 1 has no more terms to stage.
+__device__ __forceinline__ void staged_ta_store(float4* sm, int j, const float t[8]) {
+    *staged_slot(sm, 1, j, 0) = make_float4(t[0], t[1], t[2], t[3]);
+    *staged_slot(sm, 1, j, 1) = make_float4(t[4], t[5], t[6], t[7]);
+}
+__device__ __forceinline__ void staged_ta_sub(const float4* sm, int col, int j, float t[8]) {
+    const float4 a = sm[((1 * 3 + j) * 3 + 0) * STAGED_THREADS + col];
+    const float4 b = sm[((1 * 3 + j) * 3 + 1) * STAGED_THREADS + col];
+    t[0] -= a.x, t[1] -= a.y, t[2] -= a.z, t[3] -= a.w;
+    t[4] -= b.x, t[5] -= b.y, t[6] -= b.z, t[7] -= b.w;
+}
+
 __global__ void __launch_bounds__(STAGED_THREADS, 5) k_force_staged(Links<float, 6> U, Geom g, Alg<float> B, float coef,
                                                                   float alpha) {
     extern __shared__ float4 sm[];
     pdl_launch_dependents();
-    const int mu = threadIdx.x >> 5, par = blockIdx.x & 1;
-    const int h = (blockIdx.x >> 1) * 32 + (threadIdx.x & 31);
+    const int mu = threadIdx.x >> 5, par = blockIdx.x & 1, op = par ^ 1, lane = threadIdx.x & 31;
+    const int h = (blockIdx.x >> 1) * 32 + lane;
     const int hc = h < g.Vh ? h : g.Vh - 1;  // lanes past the end compute a copy and store nothing
+    const int n_own = mu < 2 ? 2 : 1;       // owned planes: nu = mu + 1, mu + 2 (mod 4)
+    const int n_terms = 3 + n_own;
     int x[4];
     cb_coords(g, par, hc, x);
+    const Hops H = make_hops(g, x);
+    const int fmu = pick(H.fwd, mu);
+    const int hpm = (H.lex + fmu) >> 1;
+    int hmn[3], hpm_mn[3], nus[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const int nu = i < mu ? i : i + 1;
+        nus[i] = nu;
+        hmn[i] = (H.lex + pick(H.bwd, nu)) >> 1;
+        hpm_mn[i] = (H.lex + fmu + pick(H.bwd, nu)) >> 1;
+    }
+    int own_nu[2], own_hpn[2];
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+        own_nu[j] = (mu + 1 + j) & 3;
+        own_hpn[j] = (H.lex + pick(H.fwd, own_nu[j])) >> 1;
+    }
     pdl_wait();
+    // half-term k < 3: dn = (e d)^+ f, d = U_nu(x+mu-nu), e = U_mu(x-nu), f = U_nu(x-nu)
+    // for the k-th direction nu != mu; k >= 3: up = (a b^+) c^+ for owned plane
+    // j = k - 3, a = U_nu(x+mu), b = U_mu(x+nu), c = U_nu(x) (shared)
+    auto issue = [&](int k, int stage) {
+        if (k < 3) {
+            stage_link(sm, stage, 0, U, nus[k], par, hpm_mn[k]);
+            stage_link(sm, stage, 1, U, mu, op, hmn[k]);
+            stage_link(sm, stage, 2, U, nus[k], op, hmn[k]);
+        } else {
+            stage_link(sm, stage, 0, U, own_nu[k - 3], op, hpm);
+            stage_link(sm, stage, 1, U, mu, op, own_hpn[k - 3]);
+        }
+    };
+    stage_link(sm, 2, 0, U, mu, par, hc);  // the updated link, with the first half-term
+    issue(0, 0);
+    cp_async_commit();
+    issue(1, 1);
+    cp_async_commit();
+    M3<float> A;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) A.e[i][j] = mk(0.f, 0.f);
     M3<float> u;
-    // the four warps are the four directions at the same sites: U_nu(x) of the
-    // upper staple terms is the updated link of warp nu
-    const M3<float> A = staple_staged<NoWork, true>(U, g, x, hc, mu, par, sm, u);
-    if (h >= g.Vh) return;
-    const M3<float> M = mul_nn(u, A);
     float t[8];
-    ta_coeffs(M, t);
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        if (k >= n_terms) break;
+        if (k + 1 < n_terms) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        const int st = k & 1;
+        if (k < 3) {
+            M3<float> d = mul_nn_2(staged_rows(sm, st, 1), staged_full(sm, st, 0));
+            rebuild_row2(d);
+            M3<float> term = mul_dn_2(d, staged_full(sm, st, 2));
+            rebuild_row2(term);
+            acc_add(A, term);
+        } else {
+            const int j = k - 3;
+            const M3<float> ab = mul_nd_2(staged_rows(sm, st, 0), staged_full(sm, st, 1));
+            M3<float> up = mul_nd_2(ab, own_full_of(sm, own_nu[j] * 32 + lane));
+            rebuild_row2(up);
+            M3<float> P = mul_nn_2(u, up);
+            rebuild_row2(P);
+            float tp[8];
+            ta_coeffs(P, tp);
+#pragma unroll
+            for (int a = 0; a < 8; a++) t[a] += tp[a];
+            staged_ta_store(sm, j, tp);  // stage 1 stages nothing after term 3
+        }
+        if (k + 2 < n_terms) {
+            issue(k + 2, st);
+            cp_async_commit();
+        }
+        if (k == 2) {
+            // the lower terms are done: complete the updated link, publish its
+            // row 2 in the slot the upper terms leave free, and take TA(U A^dn)
+            u = staged_full(sm, 2, 0);
+            *staged_slot(sm, 0, 2, 0) = make_float4(u.e[2][0].re, u.e[2][0].im, u.e[2][1].re, u.e[2][1].im);
+            *reinterpret_cast<float2*>(staged_slot(sm, 0, 2, 1)) = make_float2(u.e[2][2].re, u.e[2][2].im);
+            ta_coeffs(mul_nn(u, A), t);
+            __syncthreads();  // every warp's updated link is staged and completed
+        }
+    }
+    __syncthreads();  // every owner's TA coefficients are in shared memory
+    // planes owned by another warp: nu = mu - 1 (its first owned plane) and,
+    // for mu >= 2, nu = mu - 2 (its second)
+    staged_ta_sub(sm, ((mu + 3) & 3) * 32 + lane, 0, t);
+    if (mu >= 2) staged_ta_sub(sm, (mu - 2) * 32 + lane, 1, t);
+    if (h >= g.Vh) return;
     float* b = B.at(mu, par, h);
     if (alpha == 0.f) {
 #pragma unroll

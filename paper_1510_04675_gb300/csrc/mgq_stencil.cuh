@@ -165,19 +165,13 @@ __device__ __forceinline__ M3<float> own_full_of(float4* sm, int col) {
 }
 
 // A = the staple of U_MU(x) (as staple_two_row, with the accumulation above);
-// u = U_MU(x) (full, row 2 rebuilt).  MU may be a run-time direction (the
-// force kernel's warps); the sub-sweeps pass a compile-time one.  SHARE: the
-// block's four warps are the four directions at the same 32 sites (the force),
-// so the factor U_nu(x) of the upper terms is the updated link that warp nu
-// staged; each thread completes its own link once, publishes row 2 in the slot
-// the upper terms leave free, and after one barrier reads the others' links
-// from shared memory instead of loading and completing them again (every
-// thread of the block must call it).
+// u = U_MU(x) (full, row 2 rebuilt).  MU may be a run-time direction; the
+// sub-sweeps pass a compile-time one.
 struct NoWork {
     __device__ void operator()() const {}
 };
 // early(): independent work that runs while the first loads are in flight.
-template <class Work = NoWork, bool SHARE = false>
+template <class Work = NoWork>
 __device__ __forceinline__ M3<float> staple_staged(const Links<float, 6>& U, const Geom& g, const int x[4], int h,
                                                    const int MU, int par, float4* sm, M3<float>& u,
                                                    Work early = Work()) {
@@ -201,7 +195,7 @@ __device__ __forceinline__ M3<float> staple_staged(const Links<float, 6>& U, con
         if ((k & 1) == 0) {
             stage_link(sm, stage, 0, U, nu, op, hpm);
             stage_link(sm, stage, 1, U, MU, op, hpn[i]);
-            if (!SHARE) stage_link(sm, stage, 2, U, nu, par, h);
+            stage_link(sm, stage, 2, U, nu, par, h);
         } else {
             stage_link(sm, stage, 0, U, nu, par, hpm_mn[i]);
             stage_link(sm, stage, 1, U, MU, op, hmn[i]);
@@ -223,23 +217,11 @@ __device__ __forceinline__ M3<float> staple_staged(const Links<float, 6>& U, con
     for (int k = 0; k < 6; k++) {
         if (k < 5) cp_async_wait<1>();
         else cp_async_wait<0>();
-        if (SHARE && k == 0) {
-            // publish the updated link's row 2 in the slot the upper terms leave free
-            const M3<float> uo = staged_full(sm, 2, 0);
-            *staged_slot(sm, 0, 2, 0) = make_float4(uo.e[2][0].re, uo.e[2][0].im, uo.e[2][1].re, uo.e[2][1].im);
-            *reinterpret_cast<float2*>(staged_slot(sm, 0, 2, 1)) = make_float2(uo.e[2][2].re, uo.e[2][2].im);
-            __syncthreads();  // every warp's updated link is staged and completed
-        }
         const int st = k & 1;
         M3<float> term;
         if ((k & 1) == 0) {
             const M3<float> t = mul_nd_2(staged_rows(sm, st, 0), staged_full(sm, st, 1));
-            if constexpr (SHARE) {
-                const int i = k >> 1, nu = i < MU ? i : i + 1;
-                term = mul_nd_2(t, own_full_of(sm, nu * 32 + (threadIdx.x & 31)));
-            } else {
-                term = mul_nd_2(t, staged_full(sm, st, 2));
-            }
+            term = mul_nd_2(t, staged_full(sm, st, 2));
         } else {
             M3<float> t = mul_nn_2(staged_rows(sm, st, 1), staged_full(sm, st, 0));
             rebuild_row2(t);
@@ -252,8 +234,7 @@ __device__ __forceinline__ M3<float> staple_staged(const Links<float, 6>& U, con
             cp_async_commit();
         }
     }
-    if constexpr (SHARE) u = own_full_of(sm, threadIdx.x);
-    else u = staged_full(sm, 2, 0);
+    u = staged_full(sm, 2, 0);
     return A;
 }
 
