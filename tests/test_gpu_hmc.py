@@ -27,7 +27,8 @@ def test_force_parity_fp64(gpu, orc, dims):
 
 
 @pytest.mark.parametrize("prec,dims", [("f32", [8, 8, 8, 8]), ("f32c12", [24, 24, 24, 24]),
-                                       ("f32c12", [6, 6, 6, 6])])   # 6^4: V/2 = 648, a partly filled 32-site band
+                                       ("f32c12", [6, 6, 6, 6]),    # 6^4: V/2 = 648, a partly filled 32-site band
+                                       ("f32c12", [2, 4, 2, 6])])   # x + nu = x - nu in directions 0 and 2
 def test_force_fp32(gpu, orc, prec, dims):
     U = orc.init_links(dims, 1, seed=4)
     lat = gpu.Lattice(dims, prec)
