@@ -35,17 +35,22 @@ template <class T> __device__ __forceinline__ M3<T> alg_matrix(const T c[8]) {
     return r;
 }
 
-template <class T> __device__ __forceinline__ M3<T> commutator(const M3<T>& a, const M3<T>& b) {
-    M3<T> ab = mul_nn(a, b), ba = mul_nn(b, a);
+// [a, b] for antihermitian a, b: b a = (a b)^+, so [a, b] = a b - (a b)^+ from
+// one product; the result is antihermitian entry by entry (r_ji = -conj(r_ij)
+// exactly, the diagonal purely imaginary).
+template <class T> __device__ __forceinline__ M3<T> commutator_ah(const M3<T>& a, const M3<T>& b) {
+    const M3<T> ab = mul_nn(a, b);
+    M3<T> r;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) ab.e[i][j] = ab.e[i][j] - ba.e[i][j];
-    return ab;
+        for (int j = 0; j < 3; j++) r.e[i][j] = ab.e[i][j] - conjg(ab.e[j][i]);
+    return r;
 }
 
-// Per link: X = c0 Z0 + c1 Z1 + c2 Z2; Xi = J(X)* Lam (series: |X| is O(eps),
-// so 12 terms reach FP64 rounding and 8 terms FP32 rounding for |X| <= 0.5);
+// Per link: X = c0 Z0 + c1 Z1 + c2 Z2; Xi = J(X)* Lam, the series summed until a
+// term drops below the precision's rounding of the partial sum (|X| is O(eps):
+// a few terms; at most 12 in FP64 and 8 in FP32, enough for |X| <= 0.5);
 // Lam <- e^{-X} Lam e^{X}.
 template <class T>
 __global__ void __launch_bounds__(128) k_dexp_adjoint(Geom g, Alg<T> Z0, Alg<T> Z1, Alg<T> Z2, T c0, T c1, T c2,
@@ -63,17 +68,22 @@ __global__ void __launch_bounds__(128) k_dexp_adjoint(Geom g, Alg<T> Z0, Alg<T> 
     const M3<T> X = alg_matrix(x);
     const M3<T> L = alg_matrix(l);
     M3<T> term = L, sum = L;
+    const T tiny = sizeof(T) == 4 ? T(3e-8) : T(5e-17);
 #pragma unroll 1
     for (int n = 1; n <= (sizeof(T) == 4 ? 8 : 12); n++) {
-        term = commutator(X, term);
+        term = commutator_ah(X, term);
         const T f = T(-1) / T(n + 1);
+        T tmax = 0, smax = 0;
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int j = 0; j < 3; j++) {
                 term.e[i][j] = scale(term.e[i][j], f);
                 sum.e[i][j] = sum.e[i][j] + term.e[i][j];
+                tmax = fmax(tmax, fmax(fabs(term.e[i][j].re), fabs(term.e[i][j].im)));
+                smax = fmax(smax, fmax(fabs(sum.e[i][j].re), fabs(sum.e[i][j].im)));
             }
+        if (tmax <= tiny * smax) break;
     }
     T xi[8];
     ta_coeffs(sum, xi);
@@ -102,7 +112,7 @@ __global__ void __launch_bounds__(128) k_exp_vjp(Geom g, Alg<T> Om, Alg<T> Gin, 
     const T tiny = sizeof(T) == 4 ? T(3e-8) : T(5e-17);
 #pragma unroll 1
     for (int n = 1; n <= 40; n++) {
-        term = commutator(X, term);
+        term = commutator_ah(X, term);
         const T f = T(-1) / T(n + 1);
         T tmax = 0, smax = 0;
 #pragma unroll
@@ -150,23 +160,8 @@ __device__ __forceinline__ M3<T> psi_at(const Alg<T>& P, int mu, int par, int h)
 // it, one it traverses backwards (as W^+) carries -Psi just after it.  Its
 // cotangent at m is -TA(U_m R), R the rest of the loop after m with one
 // insertion at a time, summed; the insertion at m itself is the self term
-// -TA(W_m A_m Psi_m).
-
-// the self term
-template <class T, int NP>
-__global__ void __launch_bounds__(128) k_flow_vjp_self(Links<T, NP> U, Geom g, Alg<T> Psi, T scl, Alg<T> Lam) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= 8 * g.Vh) return;
-    const int mp = idx / g.Vh, h = idx - mp * g.Vh, rho = mp >> 1, par = mp & 1;
-    int x[4];
-    cb_coords(g, par, h, x);
-    const M3<T> A = staple(U, g, x, h, rho, par);
-    T t[8];
-    ta_coeffs(mul_nn(mul_nn(U.load(rho, par, h), A), psi_at<T, NP>(Psi, rho, par, h)), t);
-    T* b = Lam.at(rho, par, h);
-#pragma unroll
-    for (int a = 0; a < 8; a++) b[a * Alg<T>::kStep] -= scl * t[a];
-}
+// -TA(W_m A_m Psi_m), which the two launches below add half by half (the upper
+// and the lower staples of A_m).
 
 template <class T> __device__ __forceinline__ M3<T> msub(const M3<T>& a, const M3<T>& b) {
     M3<T> r;
@@ -184,9 +179,11 @@ template <class T> __device__ __forceinline__ M3<T> msub(const M3<T>& a, const M
 //   down: m Y1 Y2 Y3,   Y1 = U_nu(y-nu+rho)^+, Y2 = U_rho(y-nu)^+, Y3 = U_nu(y-nu)
 //         R_dn = -Y1 Psi_nu(y-nu+rho) Y2 Y3 - Y1 Y2 Psi_rho(y-nu) Y3 + Y1 Y2 Psi_nu(y-nu) Y3
 // each summed by the product rule over the running prefix; SIDE 0 adds
-// scale * (-TA(U_m sum_nu R_up)), SIDE 1 scale * (-TA(U_m sum_nu R_dn)) (one
-// side per launch, directions in a rolled loop, keeps the live state in
-// registers).
+// scale * (-TA(U_m (sum_nu R_up + A_up Psi_m))), SIDE 1 the same with R_dn and
+// A_dn, A_up = sum_nu X1 X2 X3 and A_dn = sum_nu Y1 Y2 Y3 the two halves of the
+// staple (one side per launch, directions in a rolled loop, keeps the live
+// state in registers).  SIDE 0 folds X1 X2 X3 Psi_m into its last insertion
+// (both Psi at y); SIDE 1 sums A_dn and multiplies by Psi_m once.
 template <class T, int NP, int SIDE>
 __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 1 : 4) k_flow_vjp_plane(Links<T, NP> U, Geom g, Alg<T> Psi, T scl, Alg<T> Lam) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -197,11 +194,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 1 : 4) k_flow_vjp_plane(
     cb_coords(g, par, h, x);
     const Hops H = make_hops(g, x);
     const int frho = pick(H.fwd, rho);
-    M3<T> Rs;
+    M3<T> Rs, As;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) Rs.e[i][j] = mk(T(0), T(0));
+        for (int j = 0; j < 3; j++) Rs.e[i][j] = As.e[i][j] = mk(T(0), T(0));
 #pragma unroll 1
     for (int K = 0; K < 3; K++) {
     const int nu = K < rho ? K : K + 1;
@@ -215,7 +212,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 1 : 4) k_flow_vjp_plane(
         const M3<T> S2 = msub(mul_nd(mul_nn(psi_at<T, NP>(Psi, nu, op, h_pr), X1), X2d),
                               mul_nn(P2, psi_at<T, NP>(Psi, rho, op, h_pn)));
         const M3<T> X3d = U.load(nu, par, h);     // X3 = X3d^+
-        R = msub(mul_nd(S2, X3d), mul_nn(mul_nd(P2, X3d), psi_at<T, NP>(Psi, nu, par, h)));
+        // the self term's X1 X2 X3 Psi_m joins the last insertion: - X1 X2 X3 (Psi_nu(y) - Psi_m)
+        T cn[8], cm[8];
+        Psi.load(nu, par, h, cn);
+        Psi.load(rho, par, h, cm);
+#pragma unroll
+        for (int a = 0; a < 8; a++) cn[a] -= cm[a];
+        R = msub(mul_nd(S2, X3d), mul_nn(mul_nd(P2, X3d), alg_matrix(cn)));
     } else {
         const int bnu = pick(H.bwd, nu);
         const int h_mn = (H.lex + bnu) >> 1;            // y - nu        (op)
@@ -227,10 +230,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 1 : 4) k_flow_vjp_plane(
         M3<T> nS2 = mul_nd(mul_dn(Y1d, psi_at<T, NP>(Psi, nu, par, h_mn_pr)), Y2d);
         acc_add(nS2, mul_nn(P2, psi_at<T, NP>(Psi, rho, op, h_mn)));
         const M3<T> Q = msub(mul_nn(P2, psi_at<T, NP>(Psi, nu, op, h_mn)), nS2);
-        R = mul_nn(Q, U.load(nu, op, h_mn));
+        const M3<T> Y3 = U.load(nu, op, h_mn);
+        R = mul_nn(Q, Y3);
+        acc_add(As, mul_nn(P2, Y3));                 // Y1 Y2 Y3, the lower staple
     }
     acc_add(Rs, R);
     }
+    if constexpr (SIDE == 1) acc_add(Rs, mul_nn(As, psi_at<T, NP>(Psi, rho, par, h)));  // the self term's half
     T t[8];
     ta_coeffs(mul_nn(U.load(rho, par, h), Rs), t);
     T* b = Lam.at(rho, par, h);
@@ -246,7 +252,6 @@ static mgq_status flow_vjp(const mgq_lattice* lat, const void* links, const void
     dispatch_prec(lat->prec, [&]<class T, int NP>() {
         const Links<T, NP> W = links_at<T, NP>(const_cast<void*>(links), lat->dims);
         const Alg<T> P = alg_at<T>(const_cast<void*>(psi), lat->dims), L = alg_at<T>(lam, lat->dims);
-        k_flow_vjp_self<T, NP><<<nblk(8L * g.Vh, 128), 128, 0, st>>>(W, g, P, (T)scl, L);
         const int nb = nblk(8L * g.Vh, 128);
         k_flow_vjp_plane<T, NP, 0><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
         k_flow_vjp_plane<T, NP, 1><<<nb, 128, 0, st>>>(W, g, P, (T)scl, L);
