@@ -12,6 +12,7 @@ and the gradient is minus the HMC force.
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import api
@@ -38,6 +39,17 @@ class WilsonAction(torch.autograd.Function):
 
 def wilson_action(omega: torch.Tensor, lat: "api.Lattice", beta: float) -> torch.Tensor:
     return WilsonAction.apply(omega, lat, beta)
+
+
+_NO_TIMES = np.zeros(0)
+
+
+def _flow_steps(lat, eps, n):
+    """n fixed flow steps of size eps with no measurement (mgq_wilson_flow_times
+    with one step per call and no measurement times: nothing is read back, so
+    the host does not wait)."""
+    for _ in range(n):
+        api.mgq_wilson_flow_times(lat, eps, eps, _NO_TIMES)
 
 
 class FlowedObservable(torch.autograd.Function):
@@ -70,7 +82,7 @@ class FlowedObservable(torch.autograd.Function):
         while done < n_steps:
             ckpts.append((done, W.links.clone()))
             m = min(k, n_steps - done)
-            api.mgq_wilson_flow(W, eps, m, m)
+            _flow_steps(W, eps, m)
             done += m
         if observable == "S":
             value = float(beta) * 6.0 * W.volume * (1.0 - api.mgq_plaquette(W))
@@ -98,7 +110,7 @@ class FlowedObservable(torch.autograd.Function):
             starts = []
             for _ in range(m):
                 starts.append(seg.links.clone())
-                api.mgq_wilson_flow(seg, ctx.eps, 1, 2)   # one step, E/Q measured only at t = 0
+                _flow_steps(seg, ctx.eps, 1)
             for w0 in reversed(starts):
                 seg.links.copy_(w0)
                 api.mgq_wilson_flow_step_adjoint(seg, ctx.eps, lam, scratch)

@@ -208,17 +208,19 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 1 : 4) k_flow_vjp_plane(
         const int h_pn = (H.lex + pick(H.fwd, nu)) >> 1;  // y + nu   (op)
         const M3<T> X1 = U.load(nu, op, h_pr);
         const M3<T> X2d = U.load(rho, op, h_pn);  // X2 = X2d^+
-        const M3<T> P2 = mul_nd(X1, X2d);         // X1 X2
-        const M3<T> S2 = msub(mul_nd(mul_nn(psi_at<T, NP>(Psi, nu, op, h_pr), X1), X2d),
-                              mul_nn(P2, psi_at<T, NP>(Psi, rho, op, h_pn)));
         const M3<T> X3d = U.load(nu, par, h);     // X3 = X3d^+
+        const M3<T> P2 = mul_nd(X1, X2d);         // X1 X2
+        const M3<T> S = mul_nd(P2, X3d);          // X1 X2 X3, the upper staple
         // the self term's X1 X2 X3 Psi_m joins the last insertion: - X1 X2 X3 (Psi_nu(y) - Psi_m)
         T cn[8], cm[8];
         Psi.load(nu, par, h, cn);
         Psi.load(rho, par, h, cm);
 #pragma unroll
         for (int a = 0; a < 8; a++) cn[a] -= cm[a];
-        R = msub(mul_nd(S2, X3d), mul_nn(mul_nd(P2, X3d), alg_matrix(cn)));
+        // R_up + S Psi_m = Psi_nu(y+rho) S - (X1 X2 Psi_rho(y+nu)) X3 - S (Psi_nu(y) - Psi_m)
+        R = msub(msub(mul_nn(psi_at<T, NP>(Psi, nu, op, h_pr), S),
+                      mul_nd(mul_nn(P2, psi_at<T, NP>(Psi, rho, op, h_pn)), X3d)),
+                 mul_nn(S, alg_matrix(cn)));
     } else {
         const int bnu = pick(H.bwd, nu);
         const int h_mn = (H.lex + bnu) >> 1;            // y - nu        (op)
