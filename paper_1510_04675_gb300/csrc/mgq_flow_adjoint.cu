@@ -228,10 +228,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 1 : 4) k_flow_vjp_plane(
         const M3<T> Y1d = U.load(nu, par, h_mn_pr);  // Y1 = Y1d^+
         const M3<T> Y2d = U.load(rho, op, h_mn);     // Y2 = Y2d^+
         const M3<T> P2 = mul_dd(Y1d, Y2d);           // Y1 Y2
-        // -S2 = Y1 Psi_a Y2 + Y1 Y2 Psi_b;  R_dn = (Y1 Y2 Psi_c - (-S2)) Y3
-        M3<T> nS2 = mul_nd(mul_dn(Y1d, psi_at<T, NP>(Psi, nu, par, h_mn_pr)), Y2d);
-        acc_add(nS2, mul_nn(P2, psi_at<T, NP>(Psi, rho, op, h_mn)));
-        const M3<T> Q = msub(mul_nn(P2, psi_at<T, NP>(Psi, nu, op, h_mn)), nS2);
+        // R_dn = (Y1 Y2 (Psi_c - Psi_b) - Y1 Psi_a Y2) Y3, Psi_b and Psi_c both at y - nu
+        T cc[8], cb[8];
+        Psi.load(nu, op, h_mn, cc);
+        Psi.load(rho, op, h_mn, cb);
+#pragma unroll
+        for (int a = 0; a < 8; a++) cc[a] -= cb[a];
+        const M3<T> Q = msub(mul_nn(P2, alg_matrix(cc)), mul_nd(mul_dn(Y1d, psi_at<T, NP>(Psi, nu, par, h_mn_pr)), Y2d));
         const M3<T> Y3 = U.load(nu, op, h_mn);
         R = mul_nn(Q, Y3);
         acc_add(As, mul_nn(P2, Y3));                 // Y1 Y2 Y3, the lower staple
