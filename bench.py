@@ -238,9 +238,20 @@ def oracle_sample(dims, beta, seconds_hint=20.0):
     for _ in range(4):
         oracle.overrelax_sweep(U, dims)
     dt = time.perf_counter() - t0
+    # single-threaded: one (mu, parity) subset of a compound sweep (1 HB + 4 OR sub-sweeps, 5 V/2 updates)
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    oracle.heatbath_subsweep(U, dims, beta, 7, 0, 2, 1, 0, 0)
+    for _ in range(4):
+        oracle.overrelax_subsweep(U, dims, 0, 0)
+    dt1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
     return {"value": 5 * 4 * V / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one compound sweep (1 HB + 4 OR) of a hot-start {'x'.join(map(str, dims))} lattice, "
-                      f"{5 * 4 * V} link updates in {dt:.2f} s (FP64, OpenMP)"}
+                      f"{5 * 4 * V} link updates in {dt:.2f} s (FP64, OpenMP)",
+            "single_thread": {"value": 5 * (V // 2) / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"the (mu = 0, even) subset of a compound sweep: 1 heat-bath + 4 "
+                                        f"overrelaxation sub-sweeps, {5 * (V // 2)} link updates in {dt1:.2f} s"}}
 
 
 def run_reference(args, dims, world, rank):
